@@ -1,0 +1,345 @@
+"""Throughput benchmark of the random-circuit workload: n = 30 qubits, 40 layers
+of Haar-random SU(2) gates on every qubit followed by C-NOTs on 15 random
+disjoint pairs (1800 gates), complex64 state (8 GiB) by default.
+
+One step = one simulation of the whole circuit from |0...0>: qs_init_basis
+followed by the fused circuit plan (every gate of the circuit).  Prints one
+JSON line (see --help).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--dtype c64|c128]
+                  [--no-fuse] [--impl ours|reference]
+
+--impl reference times the CPU oracle (complex128, plain row-by-row gate
+application) on the host cores, on a bounded sample of the same workload.
+Under torchrun each rank runs an independent replica of the workload (its own
+seed); no data crosses ranks; value is the sum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+N_QUBITS = 30
+LAYERS = 40
+SEED = 20260515
+
+
+def amp_updates(n, gates):
+    """Amplitudes changed by each gate's definition: 2^n for a single-qubit
+    gate, 2^(n - #controls) for a controlled one."""
+    tot = 0
+    for g in gates:
+        if g.kind == "SWAP":
+            tot += 1 << (n - len(g.controls))
+        else:
+            tot += 1 << (n - len(g.controls))
+    return tot
+
+
+def workload_config(args, n_ranks):
+    return {
+        "workload": "random circuit n=%d, %d layers (Haar SU(2) on every qubit + C-NOTs on %d disjoint pairs), %s state"
+                    % (N_QUBITS, LAYERS, N_QUBITS // 2, "complex64" if args.dtype == "c64" else "complex128"),
+        "n_qubits": N_QUBITS, "layers": LAYERS, "gates": LAYERS * (N_QUBITS + N_QUBITS // 2),
+        "state_bytes": (8 if args.dtype == "c64" else 16) << N_QUBITS,
+        "fused": not args.no_fuse,
+        "l2": "state (>= 8 GiB) larger than L2 (129 MB); no flush needed",
+        "parallelism": "replicas%d" % n_ranks,
+    }
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if p[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs"), "measured"
+    return 6800.0, "fallback"
+
+
+def cpu_baseline(dtype, budget_s=20.0):
+    """The oracle (complex128, row-by-row, OpenMP over rows) on the host cores,
+    on a bounded prefix of the same circuit.  n = 30 when the host has room
+    for the state and its out-of-place copy (2 x 16 GiB), else n = 26."""
+    import oracle
+    try:
+        with open("/proc/meminfo") as f:
+            avail = int([l for l in f if l.startswith("MemAvailable")][0].split()[1]) * 1024
+    except Exception:
+        avail = 0
+    n = N_QUBITS if avail > 48 * (1 << 30) else 26
+    gates = W.random_circuit(n, LAYERS, seed=SEED)
+    psi = oracle.basis(n, 0)
+    done, upd = 0, 0
+    t0 = time.perf_counter()
+    for g in gates:
+        psi = oracle.run(n, [g], psi=psi)
+        done += 1
+        upd += amp_updates(n, [g])
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    del psi
+    return {"value": upd / dt, "unit": "amp-updates/s", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": "first %d of %d gates of the workload at n=%d (complex128, OpenMP rows), %.1f s"
+                      % (done, len(gates), n, dt)}
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the oracle as the reference arm (rank 0 only)."""
+    if rank != 0:
+        return
+    steps = []
+    base = None
+    for k in range(args.warmup + args.steps):
+        b = cpu_baseline(args.dtype, budget_s=args.ref_budget)
+        if k >= args.warmup:
+            steps.append(b)
+        base = b
+    val = statistics.median([s["value"] for s in steps])
+    line = {
+        "impl": "reference", "metric": "amp-updates/s", "value": val, "unit": "amp-updates/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic", "config": workload_config(args, world),
+        "cpu_baseline": {"value": val, "unit": "amp-updates/s", "cores": base["cores"],
+                         "kind": "oracle", "sample": base["sample"]},
+        "e2e": {"value": val, "unit": "amp-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--dtype", choices=["c64", "c128"], default="c64")
+    ap.add_argument("--no-fuse", action="store_true")
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--ref-budget", type=float, default=15.0)
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    import paper_quant_ph_0201042_gb300 as qs
+    from paper_quant_ph_0201042_gb300 import build as qbuild
+    qbuild.build()
+
+    n = N_QUBITS
+    gates = W.random_circuit(n, LAYERS, seed=SEED + rank)
+    upd = amp_updates(n, gates)
+    plan = qs.Plan(n, args.dtype, gates, fuse=not args.no_fuse)
+    state = qs.State(n, args.dtype)
+    amp_bytes = 8 if args.dtype == "c64" else 16
+
+    def step():
+        state.init_basis(0)
+        plan.execute(state)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # timed region: device events on the launching stream, plus per-launch
+    # events recorded by the library around every pass
+    plan.set_timing(True)
+    plan.timing()
+    stream = torch.cuda.current_stream()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    ev0.record(stream)
+    kern_ms, kern_n = 0.0, 0
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    if dist:
+        dist.barrier()
+    ms, nl = plan.timing()
+    kern_ms += ms
+    kern_n += nl
+    plan.set_timing(False)
+    total_ms = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * upd / (ms_per_step / 1e3)
+
+    # roofline of the dominant kernel (the fused pass, or the pair sweep)
+    peak_gbs, peak_src = measured_peaks()
+    per_launch_ms = kern_ms / max(1, kern_n)
+    bytes_per_launch = 2 * (amp_bytes << n)   # one read and one write of the state
+    achieved = bytes_per_launch / (per_launch_ms / 1e3) / 1e9
+    if args.no_fuse:
+        # unfused: algorithmic bytes = 2 x touched amplitudes per gate
+        tb = sum(2 * amp_bytes * (1 << (n - len(g.controls))) for g in gates)
+        achieved = tb * args.steps / (kern_ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
+            "frac": achieved / peak_gbs if peak_gbs else None, "traffic": None,
+            "kernel": "k_fused" if not args.no_fuse else "k_pair",
+            "peak_source": peak_src, "launches_timed": kern_n, "kernel_ms_per_step": kern_ms / args.steps}
+    # FP32/FP64 multiply-add work of the circuit, for the ALU view of the same kernel
+    fma_per_amp = 8
+    n1q = sum(1 for g in gates if g.kind == "MATRIX")
+    flops = 2 * fma_per_amp * n1q * (1 << n)
+    roof["alu_tflops"] = flops * args.steps / (kern_ms / 1e3) / 1e12
+
+    line = {
+        "metric": "amp-updates/s", "value": value, "unit": "amp-updates/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if args.dtype == "c64" else "f64",
+        "data": "synthetic", "config": workload_config(args, world),
+        "gates_per_s": world * len(gates) / (ms_per_step / 1e3),
+        "hbm_gbs_algorithmic": world * plan.launches * bytes_per_launch / (ms_per_step / 1e3) / 1e9
+        if not args.no_fuse else None,
+        "passes_per_step": plan.launches,
+        "roofline": roof,
+        "gpu_launches": args.steps * (plan.launches + 1),
+        "clocks": clocks,
+    }
+
+    # end to end through the public API with host buffers: the gate list goes
+    # in from host memory (qs_apply_circuit copies, plans and launches), the
+    # final state comes back to pinned host memory (qs_copy_out)
+    if not args.no_e2e:
+        host = torch.empty(1 << n, dtype=torch.complex64 if args.dtype == "c64" else torch.complex128,
+                           pin_memory=True)
+        hbuf = host.numpy()
+        import ctypes
+        garr = qs.gates_to_abi(gates)
+        opts = qs._opts(not args.no_fuse)
+
+        def e2e_step():
+            qs.check(qs.lib().qs_init_basis(state.handle, 0))
+            qs.check(qs.lib().qs_apply_circuit(state.handle, garr, len(gates), ctypes.byref(opts)))
+            qs.check(qs.lib().qs_copy_out(state.handle, hbuf.ctypes.data_as(ctypes.c_void_p), hbuf.nbytes))
+
+        e2e_step()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        k = max(1, min(args.steps, 3))
+        for _ in range(k):
+            e2e_step()
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / k
+        if dist:
+            t = torch.tensor([dt], dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        line["e2e"] = {"value": world * upd / dt, "unit": "amp-updates/s",
+                       "h2d_bytes_per_step": ctypes.sizeof(garr), "d2h_bytes_per_step": hbuf.nbytes,
+                       "ms_per_step": dt * 1e3, "steps": k}
+        del host
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        del state
+        torch.cuda.empty_cache()
+        line["cpu_baseline"] = cpu_baseline(args.dtype)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,234 @@
+/*
+ * qsim.h -- C ABI of the GB300 state-vector simulator.
+ *
+ * The method is that of Niwa, Matsumoto and Imai, "General-Purpose Parallel
+ * Simulator for Quantum Computing" (quant-ph/0201042):
+ *   - Sec. 2.1: an n-qubit register is a vector of 2^n complex amplitudes;
+ *   - Sec. 2.2.1: a single-qubit gate U on qubit q updates the amplitude
+ *     pairs (x, y) = (alpha[i0], alpha[i0 + s]), s = 2^(n-1-q), bit n-1-q of
+ *     i0 clear, as x' = u11 x + u12 y, y' = u21 x + u22 y; qubit 0 is the most
+ *     significant bit of the index;
+ *   - Sec. 2.2.2: a controlled gate updates only the pairs whose control bits
+ *     hold ("many controlled bit cases" and the f-controlled gate are the
+ *     same rule with more control bits);
+ *   - Sec. 3: decoherence (Pauli flips) and operational errors (Gaussian
+ *     deviations of gate angles), simulated as pure-state trajectories.
+ *
+ * Conventions for every call:
+ *   - Qubit indices are in [0, n); qubit q is index bit n-1-q.  Control masks
+ *     are in qubit order: bit q of ctrl_mask set means qubit q is a control,
+ *     and bit q of ctrl_val is the value it must hold.
+ *   - Gate matrices cross the ABI in double precision (qs_c128), row major
+ *     u11, u12, u21, u22, whatever the dtype of the state; a complex64 state
+ *     is updated in single precision with the matrix rounded to single.
+ *   - Amplitudes are stored interleaved (re, im): 8 bytes each for QS_C64,
+ *     16 bytes each for QS_C128, amplitude i at byte offset i * size.
+ *   - Calls that modify a state are asynchronous on the state's stream (the
+ *     legacy default stream until qs_set_stream).  Calls that return a number
+ *     to the host (qs_prob, qs_norm, ...) synchronise that stream.
+ *   - Every call returns a qs_status; QS_OK is 0.  On failure the state is
+ *     left as it was when the error is detected on the host (argument
+ *     errors), and qs_last_error() returns a message for the calling thread.
+ *     No C++ exception crosses this boundary.
+ *   - The library does not fall back to any CPU computation: every gate and
+ *     every reduction runs in the library's CUDA kernels.
+ */
+#ifndef QSIM_H
+#define QSIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    QS_OK = 0,
+    QS_EINVAL = 1,        /* bad argument (qubit out of range, target among controls, ...) */
+    QS_ERANGE = 2,        /* size out of range (n > QS_MAX_QUBITS, index >= 2^n, bytes mismatch) */
+    QS_ENOMEM = 3,        /* device or pinned host allocation failed */
+    QS_ECUDA = 4,         /* a CUDA runtime call or kernel launch failed */
+    QS_ETIMEOUT = 5,      /* a bounded device-side wait gave up */
+    QS_EUNSUPPORTED = 6   /* valid request this build does not implement */
+} qs_status;
+
+typedef enum { QS_C64 = 1, QS_C128 = 2 } qs_dtype;
+
+#define QS_MAX_QUBITS 40
+
+typedef struct { double re, im; } qs_c128;
+
+typedef struct qs_state qs_state;   /* opaque; created by qs_alloc / qs_wrap, released by qs_free */
+typedef struct qs_plan qs_plan;     /* opaque compiled circuit; released by qs_plan_free */
+
+/* Gate kinds.  Angles are in radians.  Paper references: H (Sec. 2.3.1),
+ * U_R, U_P1, U_P2 (Sec. 3.2), Pauli X, Y, Z (Sec. 3.1). */
+typedef enum {
+    QS_GATE_MATRIX = 0,  /* explicit u[0..3] */
+    QS_GATE_H = 1,       /* (1/sqrt 2) [[1, 1], [1, -1]] */
+    QS_GATE_X = 2,       /* NOT; with one control: C-NOT */
+    QS_GATE_Y = 3,
+    QS_GATE_Z = 4,
+    QS_GATE_UP1 = 5,     /* U_P1(theta[0]) = diag(1, e^{i phi}); controlled: the phase shift R_k */
+    QS_GATE_UP2 = 6,     /* U_P2(theta[0]) = diag(e^{i phi}, 1) */
+    QS_GATE_UR = 7,      /* U_R(theta[0]) = [[cos, -sin], [sin, cos]] */
+    QS_GATE_URP1 = 8,    /* U_R(theta[0]) U_P1(theta[1]); H = URP1(pi/4, pi), NOT = URP1(pi/2, pi) */
+    QS_GATE_RY = 9,      /* exp(-i theta[0] Y / 2) */
+    QS_GATE_RZ = 10,     /* exp(-i theta[0] Z / 2) */
+    QS_GATE_SWAP = 11    /* exchange qubits t and t2 */
+} qs_gate_kind;
+
+/* One gate of a circuit (112 bytes). */
+typedef struct {
+    int32_t kind;        /* qs_gate_kind */
+    int32_t t;           /* target qubit */
+    int32_t t2;          /* second qubit of QS_GATE_SWAP, otherwise ignored (set -1) */
+    int32_t param;       /* index of theta[0] in a parameter vector for differentiation,
+                            -1 if the gate is not differentiated; URP1 also uses param+1 */
+    uint64_t ctrl_mask;  /* qubit-order control mask; must not contain t (or t2) */
+    uint64_t ctrl_val;   /* required control values (bits outside ctrl_mask ignored) */
+    double theta[2];     /* angles of the kind */
+    qs_c128 u[4];        /* matrix of QS_GATE_MATRIX, row major; ignored otherwise */
+} qs_gate;
+
+/* Execution options of qs_apply_circuit / qs_plan_create.  A zeroed struct
+ * (or NULL) selects the defaults. */
+typedef struct {
+    int32_t no_fusion;       /* 1: one unfused pair-sweep launch per gate (the plain
+                                per-gate path); 0: fuse runs of gates into tile passes */
+    int32_t max_ops_per_pass;/* 0: default */
+    int32_t reserved[6];
+} qs_exec_opts;
+
+/* --------------------------------------------------------------------- */
+/* State lifetime                                                          */
+/* --------------------------------------------------------------------- */
+
+/* Allocates a 2^n-amplitude state on the current CUDA device, owned by the
+ * library (freed by qs_free), and initialises it to |0...0>.
+ * Errors: QS_ERANGE if n < 1 or n > QS_MAX_QUBITS, QS_EINVAL for a bad
+ * dtype or NULL out, QS_ENOMEM if the device allocation fails. */
+qs_status qs_alloc(int n, qs_dtype dt, qs_state **out);
+
+/* Wraps caller-owned device memory (e.g. a torch tensor) of 2^n amplitudes
+ * of dtype dt as a state.  The memory must stay valid until qs_free, which
+ * never frees it; it must be 16-byte aligned.  Contents are not modified.
+ * Errors: as qs_alloc, QS_EINVAL for a NULL or misaligned pointer. */
+qs_status qs_wrap(void *dev_ptr, int n, qs_dtype dt, qs_state **out);
+
+/* Releases the state (and, for qs_alloc states, its device memory) after
+ * synchronising its stream.  NULL is accepted. */
+qs_status qs_free(qs_state *s);
+
+/* All later operations on s are enqueued on `stream` (a cudaStream_t; NULL
+ * selects the legacy default stream). */
+qs_status qs_set_stream(qs_state *s, void *stream);
+
+/* Device pointer, qubit count and dtype of a state (any out may be NULL). */
+qs_status qs_info(const qs_state *s, void **dev_ptr, int *n, qs_dtype *dt);
+
+/* --------------------------------------------------------------------- */
+/* Evolution steps, Sec. 2.2                                               */
+/* --------------------------------------------------------------------- */
+
+/* |x>: amplitude x set to 1, all others to 0.  QS_ERANGE if x >= 2^n. */
+qs_status qs_init_basis(qs_state *s, uint64_t x);
+
+/* Single-qubit gate U on qubit q (Sec. 2.2.1): every pair (i0, i0 + 2^(n-1-q))
+ * is updated in place by one thread that reads both amplitudes before it
+ * writes either.  QS_EINVAL if q is out of range or U is NULL. */
+qs_status qs_apply_1q(qs_state *s, int q, const qs_c128 U[4]);
+
+/* Controlled gate (Sec. 2.2.2): U on target t for the pairs whose control
+ * qubit c is 1.  QS_EINVAL if c == t or either is out of range. */
+qs_status qs_apply_ctrl(qs_state *s, int c, int t, const qs_c128 U[4]);
+
+/* Many-control gate (Sec. 2.2.2, also the f-controlled gate with f an index
+ * predicate): U on target t for the pairs whose control qubits (ctrl_mask)
+ * hold the values ctrl_val.  Only the matching pairs are visited, so a gate
+ * with n-1 controls touches two amplitudes.  QS_EINVAL if ctrl_mask contains
+ * t or a qubit >= n. */
+qs_status qs_apply_mctrl(qs_state *s, uint64_t ctrl_mask, uint64_t ctrl_val, int t,
+                         const qs_c128 U[4]);
+
+/* SWAP of qubits a and b (a != b). */
+qs_status qs_apply_swap(qs_state *s, int a, int b);
+
+/* One gate of any kind, unfused. */
+qs_status qs_apply_gate(qs_state *s, const qs_gate *g);
+
+/* Applies the m gates in order.  With fusion (the default) consecutive gates
+ * are grouped into passes that each read and write the state once: a pass
+ * keeps a tile of 2^k amplitudes (the low index bits plus a chosen set of
+ * high bits) in registers and shared memory and applies every gate of the
+ * group to it.  Gates are validated and copied before the call returns. */
+qs_status qs_apply_circuit(qs_state *s, const qs_gate *g, size_t m, const qs_exec_opts *opts);
+
+/* Compiles a circuit for n qubits and dtype dt once (validation, fusion
+ * planning, gate tables uploaded to the device) so that it can be executed
+ * many times.  The plan is bound to the device that was current. */
+qs_status qs_plan_create(int n, qs_dtype dt, const qs_gate *g, size_t m,
+                         const qs_exec_opts *opts, qs_plan **out);
+
+/* Executes a plan on a state of matching n and dtype, on the state's stream.
+ * QS_EINVAL on a size or dtype mismatch. */
+qs_status qs_plan_execute(qs_state *s, const qs_plan *p);
+
+/* Number of kernel launches one execution makes and the number of gates;
+ * either pointer may be NULL. */
+qs_status qs_plan_info(const qs_plan *p, int64_t *n_launches, int64_t *n_gates);
+
+qs_status qs_plan_free(qs_plan *p);
+
+/* Per-launch timing of plan executions, for roofline measurement.  While
+ * enabled, qs_plan_execute records a CUDA event pair on the state's stream
+ * around every kernel launch it makes; qs_plan_timing waits for the recorded
+ * events, returns the summed device time (ms) and the number of timed
+ * launches since the previous read, and clears them.  Disabled by default;
+ * enabling allocates the events lazily (QS_ECUDA if that fails).  Not
+ * thread-safe with respect to concurrent executions of the same plan. */
+qs_status qs_plan_set_timing(qs_plan *p, int enable);
+qs_status qs_plan_timing(qs_plan *p, double *kernel_ms, int64_t *n_launches);
+
+/* --------------------------------------------------------------------- */
+/* Reductions, accumulated in double precision for both dtypes             */
+/* --------------------------------------------------------------------- */
+
+/* |alpha_index|^2.  QS_ERANGE if index >= 2^n. */
+qs_status qs_prob(qs_state *s, uint64_t index, double *out);
+
+/* Probability that qubit q reads 1. */
+qs_status qs_prob_qubit(qs_state *s, int q, double *p1);
+
+/* <psi| P |psi> for the Pauli string P: exactly n characters from
+ * {'I','X','Y','Z'}, character q acting on qubit q.  QS_EINVAL otherwise. */
+qs_status qs_expect(qs_state *s, const char *pauli, double *out);
+
+/* <a|b> = sum_i conj(a_i) b_i.  a and b must have the same n and dtype and
+ * the same stream.  QS_EINVAL otherwise. */
+qs_status qs_inner(qs_state *a, qs_state *b, qs_c128 *out);
+
+/* sum_i |alpha_i|^2. */
+qs_status qs_norm(qs_state *s, double *out);
+
+/* Divides the state by the square root of its (double precision) norm. */
+qs_status qs_renormalize(qs_state *s);
+
+/* --------------------------------------------------------------------- */
+/* Host copies (checkpoint / restore)                                      */
+/* --------------------------------------------------------------------- */
+
+/* Copies the whole state to / from host memory (pinned or pageable).  bytes
+ * must equal 2^n times the amplitude size, else QS_ERANGE.  Synchronous. */
+qs_status qs_copy_out(qs_state *s, void *host, size_t bytes);
+qs_status qs_copy_in(qs_state *s, const void *host, size_t bytes);
+
+/* Thread-local message describing the last failure of this thread. */
+const char *qs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QSIM_H */

@@ -1,0 +1,316 @@
+"""Python binding of libqsim, the GB300 state-vector simulator of the method of
+quant-ph/0201042 (Niwa, Matsumoto, Imai).
+
+Argument marshalling only: every gate, reduction and trajectory runs in the
+CUDA kernels of libqsim.so behind the C ABI of include/qsim.h.  PyTorch
+provides the device memory (a state is a torch complex tensor wrapped with
+qs_wrap) and the stream (the current torch stream).  There is no CPU fallback:
+if the library has not been built, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Iterable, Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libqsim.so")
+
+QS_C64 = 1
+QS_C128 = 2
+DTYPES = {"c64": QS_C64, "c128": QS_C128}
+KIND_CODES = {
+    "MATRIX": 0, "H": 1, "X": 2, "Y": 3, "Z": 4, "UP1": 5, "UP2": 6,
+    "UR": 7, "URP1": 8, "RY": 9, "RZ": 10, "SWAP": 11,
+}
+STATUS = {0: "QS_OK", 1: "QS_EINVAL", 2: "QS_ERANGE", 3: "QS_ENOMEM", 4: "QS_ECUDA",
+          5: "QS_ETIMEOUT", 6: "QS_EUNSUPPORTED"}
+
+
+class QsimError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+class C128(ctypes.Structure):
+    _fields_ = [("re", ctypes.c_double), ("im", ctypes.c_double)]
+
+
+class QsGate(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int32), ("t", ctypes.c_int32), ("t2", ctypes.c_int32),
+        ("param", ctypes.c_int32), ("ctrl_mask", ctypes.c_uint64), ("ctrl_val", ctypes.c_uint64),
+        ("theta", ctypes.c_double * 2), ("u", C128 * 4),
+    ]
+
+
+class QsExecOpts(ctypes.Structure):
+    _fields_ = [("no_fusion", ctypes.c_int32), ("max_ops_per_pass", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
+
+
+assert ctypes.sizeof(QsGate) == 112
+
+_lib: Optional[ctypes.CDLL] = None
+
+# exported entry points and their argument types
+_SIGS = {
+    "qs_alloc": [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)],
+    "qs_wrap": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)],
+    "qs_free": [ctypes.c_void_p],
+    "qs_set_stream": [ctypes.c_void_p, ctypes.c_void_p],
+    "qs_info": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int),
+                ctypes.POINTER(ctypes.c_int)],
+    "qs_init_basis": [ctypes.c_void_p, ctypes.c_uint64],
+    "qs_apply_1q": [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(C128)],
+    "qs_apply_ctrl": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(C128)],
+    "qs_apply_mctrl": [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
+                       ctypes.POINTER(C128)],
+    "qs_apply_swap": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int],
+    "qs_apply_gate": [ctypes.c_void_p, ctypes.POINTER(QsGate)],
+    "qs_apply_circuit": [ctypes.c_void_p, ctypes.POINTER(QsGate), ctypes.c_size_t,
+                         ctypes.POINTER(QsExecOpts)],
+    "qs_plan_create": [ctypes.c_int, ctypes.c_int, ctypes.POINTER(QsGate), ctypes.c_size_t,
+                       ctypes.POINTER(QsExecOpts), ctypes.POINTER(ctypes.c_void_p)],
+    "qs_plan_execute": [ctypes.c_void_p, ctypes.c_void_p],
+    "qs_plan_info": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
+    "qs_plan_free": [ctypes.c_void_p],
+    "qs_plan_set_timing": [ctypes.c_void_p, ctypes.c_int],
+    "qs_plan_timing": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)],
+    "qs_prob": [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)],
+    "qs_prob_qubit": [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)],
+    "qs_expect": [ctypes.c_void_p, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double)],
+    "qs_inner": [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(C128)],
+    "qs_norm": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)],
+    "qs_renormalize": [ctypes.c_void_p],
+    "qs_copy_out": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t],
+    "qs_copy_in": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t],
+}
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libqsim.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libqsim.so is not built (run __graft_entry__.build() or "
+                           "python -m paper_quant_ph_0201042_gb300.build)")
+    L = ctypes.CDLL(LIB_PATH)
+    for name, args in _SIGS.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    L.qs_last_error.argtypes = []
+    L.qs_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def check(st: int) -> None:
+    if st != 0:
+        raise QsimError(st, lib().qs_last_error().decode(errors="replace"))
+
+
+def _mat(U) -> ctypes.Array:
+    m = np.asarray(U, dtype=np.complex128).reshape(4)
+    return (C128 * 4)(*[C128(float(z.real), float(z.imag)) for z in m])
+
+
+def gates_to_abi(gates: Sequence) -> ctypes.Array:
+    """Marshals gate descriptions (objects with kind, target, target2, controls,
+    angles, matrix, param) into a qs_gate array."""
+    arr = (QsGate * max(1, len(gates)))()
+    for i, g in enumerate(gates):
+        c = arr[i]
+        c.kind = KIND_CODES[g.kind]
+        c.t = g.target
+        c.t2 = g.target2
+        c.param = g.param
+        cm = cv = 0
+        for q, v in g.controls.items():
+            cm |= 1 << q
+            if v:
+                cv |= 1 << q
+        c.ctrl_mask = cm
+        c.ctrl_val = cv
+        for k, a in enumerate(g.angles):
+            c.theta[k] = a
+        if g.matrix is not None:
+            m = np.asarray(g.matrix, dtype=np.complex128).reshape(4)
+            for k in range(4):
+                c.u[k].re = float(m[k].real)
+                c.u[k].im = float(m[k].imag)
+    return arr
+
+
+def _opts(fuse: bool, max_ops: int = 0) -> QsExecOpts:
+    o = QsExecOpts()
+    o.no_fusion = 0 if fuse else 1
+    o.max_ops_per_pass = max_ops
+    return o
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("no CUDA device: libqsim runs only on the GPU")
+    return torch
+
+
+class State:
+    """An n-qubit register on the current CUDA device, held in a torch tensor
+    (complex64 or complex128, 2^n elements) and wrapped by qs_wrap.  All
+    operations are enqueued on the torch stream that is current when the
+    state is created (or on `stream`)."""
+
+    def __init__(self, n: int, dtype: str = "c64", tensor=None, stream=None):
+        torch = _torch()
+        self.n = n
+        self.dtype = dtype
+        tdt = torch.complex64 if dtype == "c64" else torch.complex128
+        if tensor is None:
+            tensor = torch.empty(1 << n, dtype=tdt, device="cuda")
+        assert tensor.dtype == tdt and tensor.numel() == (1 << n) and tensor.is_contiguous()
+        self.tensor = tensor
+        self._h = ctypes.c_void_p()
+        check(lib().qs_wrap(ctypes.c_void_p(tensor.data_ptr()), n, DTYPES[dtype], ctypes.byref(self._h)))
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self.stream = s
+        check(lib().qs_set_stream(self._h, ctypes.c_void_p(s.cuda_stream)))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            lib().qs_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # evolution
+    def init_basis(self, x: int = 0):
+        check(lib().qs_init_basis(self._h, x))
+        return self
+
+    def apply_1q(self, q: int, U):
+        check(lib().qs_apply_1q(self._h, q, _mat(U)))
+        return self
+
+    def apply_ctrl(self, c: int, t: int, U):
+        check(lib().qs_apply_ctrl(self._h, c, t, _mat(U)))
+        return self
+
+    def apply_mctrl(self, ctrl_mask: int, ctrl_val: int, t: int, U):
+        check(lib().qs_apply_mctrl(self._h, ctrl_mask, ctrl_val, t, _mat(U)))
+        return self
+
+    def apply_swap(self, a: int, b: int):
+        check(lib().qs_apply_swap(self._h, a, b))
+        return self
+
+    def apply_gate(self, g):
+        arr = gates_to_abi([g])
+        check(lib().qs_apply_gate(self._h, arr))
+        return self
+
+    def apply_circuit(self, gates: Sequence, fuse: bool = True, max_ops: int = 0):
+        arr = gates_to_abi(gates)
+        o = _opts(fuse, max_ops)
+        check(lib().qs_apply_circuit(self._h, arr, len(gates), ctypes.byref(o)))
+        return self
+
+    # reductions (double precision)
+    def prob(self, index: int) -> float:
+        r = ctypes.c_double()
+        check(lib().qs_prob(self._h, index, ctypes.byref(r)))
+        return r.value
+
+    def prob_qubit(self, q: int) -> float:
+        r = ctypes.c_double()
+        check(lib().qs_prob_qubit(self._h, q, ctypes.byref(r)))
+        return r.value
+
+    def expect(self, pauli: str) -> float:
+        r = ctypes.c_double()
+        check(lib().qs_expect(self._h, pauli.encode(), ctypes.byref(r)))
+        return r.value
+
+    def inner(self, other: "State") -> complex:
+        r = C128()
+        check(lib().qs_inner(self._h, other._h, ctypes.byref(r)))
+        return complex(r.re, r.im)
+
+    def norm(self) -> float:
+        r = ctypes.c_double()
+        check(lib().qs_norm(self._h, ctypes.byref(r)))
+        return r.value
+
+    def renormalize(self):
+        check(lib().qs_renormalize(self._h))
+        return self
+
+    # host copies
+    def to_numpy(self) -> np.ndarray:
+        out = np.empty(1 << self.n, dtype=np.complex64 if self.dtype == "c64" else np.complex128)
+        check(lib().qs_copy_out(self._h, out.ctypes.data_as(ctypes.c_void_p), out.nbytes))
+        return out
+
+    def from_numpy(self, arr: np.ndarray):
+        a = np.ascontiguousarray(arr, dtype=np.complex64 if self.dtype == "c64" else np.complex128)
+        assert a.size == 1 << self.n
+        check(lib().qs_copy_in(self._h, a.ctypes.data_as(ctypes.c_void_p), a.nbytes))
+        return self
+
+
+class Plan:
+    """A circuit compiled once (validation, fusion planning) for repeated
+    execution on states of n qubits and the given dtype."""
+
+    def __init__(self, n: int, dtype: str, gates: Sequence, fuse: bool = True, max_ops: int = 0):
+        self.n = n
+        self.dtype = dtype
+        arr = gates_to_abi(gates)
+        o = _opts(fuse, max_ops)
+        self._h = ctypes.c_void_p()
+        check(lib().qs_plan_create(n, DTYPES[dtype], arr, len(gates), ctypes.byref(o),
+                                   ctypes.byref(self._h)))
+        nl = ctypes.c_int64()
+        ng = ctypes.c_int64()
+        check(lib().qs_plan_info(self._h, ctypes.byref(nl), ctypes.byref(ng)))
+        self.launches = nl.value
+        self.n_gates = ng.value
+
+    def execute(self, state: State):
+        check(lib().qs_plan_execute(state.handle, self._h))
+        return state
+
+    def set_timing(self, on: bool = True):
+        check(lib().qs_plan_set_timing(self._h, 1 if on else 0))
+
+    def timing(self):
+        """(summed device ms, launches) of the launches timed since the last read."""
+        ms = ctypes.c_double()
+        nl = ctypes.c_int64()
+        check(lib().qs_plan_timing(self._h, ctypes.byref(ms), ctypes.byref(nl)))
+        return ms.value, nl.value
+
+    def close(self):
+        if self._h:
+            lib().qs_plan_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

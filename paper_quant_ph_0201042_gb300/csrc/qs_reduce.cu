@@ -1,0 +1,178 @@
+// Reductions over the register in double precision: the norm (Sec. 2.1 unit
+// length), the probability of one basis state or of one qubit reading 1 (the
+// |0><0| term of Sec. 4.3.1, the amplitude of the marked element of Sec. 5.3),
+// Pauli expectation values and inner products (the fidelity of Sec. 5.2).
+//
+// Two deterministic levels: RED_BLOCKS blocks each sum a fixed grid-stride
+// slice of the vector (double accumulators, fixed shuffle tree), then one block
+// sums the RED_BLOCKS partials in a fixed order.  The result stays on the
+// device (s->result) and is copied to pinned host memory by the caller.
+#include "qs_internal.cuh"
+
+namespace qs {
+
+namespace {
+
+__device__ __forceinline__ double2 warp_sum(double2 v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    }
+    return v;
+}
+
+// Block-wide sum in a fixed order; valid in thread 0.
+__device__ __forceinline__ double2 block_sum(double2 v) {
+    __shared__ double2 sh[32];
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        const int nw = blockDim.x >> 5;
+        v = l < nw ? sh[l] : make_double2(0.0, 0.0);
+        v = warp_sum(v);
+    }
+    return v;
+}
+
+template <typename R>
+__device__ __forceinline__ double2 ld(const cplx<R> *a, uint64_t i) {
+    const cplx<R> v = a[i];
+    return make_double2(double(v.x), double(v.y));
+}
+
+// kind RED_NORM: sum |a_i|^2
+// kind RED_PROB_BIT: sum over i with (i & arg0) != 0 of |a_i|^2
+// kind RED_PAULI: sum_i conj(a[i ^ arg0]) a[i] (-1)^popcount(i & arg1)
+// kind RED_INNER: sum_i conj(a_i) b_i
+template <typename R, int KIND>
+__global__ void __launch_bounds__(RED_THREADS) k_partial(const cplx<R> *__restrict__ a,
+                                                         const cplx<R> *__restrict__ b, uint64_t N,
+                                                         uint64_t arg0, uint64_t arg1,
+                                                         double2 *__restrict__ partial) {
+    double2 acc = make_double2(0.0, 0.0);
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += stride) {
+        const double2 v = ld<R>(a, i);
+        if (KIND == RED_NORM) {
+            acc.x = fma(v.x, v.x, acc.x);
+            acc.x = fma(v.y, v.y, acc.x);
+        } else if (KIND == RED_PROB_BIT) {
+            if (i & arg0) {
+                acc.x = fma(v.x, v.x, acc.x);
+                acc.x = fma(v.y, v.y, acc.x);
+            }
+        } else if (KIND == RED_PAULI) {
+            const double2 w = ld<R>(a, i ^ arg0);
+            const double sg = (__popcll(i & arg1) & 1) ? -1.0 : 1.0;
+            // conj(w) * v
+            acc.x = fma(sg, w.x * v.x + w.y * v.y, acc.x);
+            acc.y = fma(sg, w.x * v.y - w.y * v.x, acc.y);
+        } else {  // RED_INNER: conj(v) * w
+            const double2 w = ld<R>(b, i);
+            acc.x += v.x * w.x + v.y * w.y;
+            acc.y += v.x * w.y - v.y * w.x;
+        }
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+// Sums the partials in a fixed order; multiplies by i^phase_quarter.
+__global__ void __launch_bounds__(RED_THREADS) k_final(const double2 *__restrict__ partial, int np,
+                                                       int phase_quarter, double2 *__restrict__ out) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int k = threadIdx.x; k < np; k += blockDim.x) {
+        acc.x += partial[k].x;
+        acc.y += partial[k].y;
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) {
+        double2 r = acc;
+        switch (phase_quarter & 3) {
+        case 1: r = make_double2(-acc.y, acc.x); break;
+        case 2: r = make_double2(-acc.x, -acc.y); break;
+        case 3: r = make_double2(acc.y, -acc.x); break;
+        default: break;
+        }
+        out[0] = r;
+    }
+}
+
+template <typename R>
+__global__ void k_prob_index(const cplx<R> *__restrict__ a, uint64_t x, double2 *out) {
+    const double2 v = ld<R>(a, x);
+    out[0] = make_double2(v.x * v.x + v.y * v.y, 0.0);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_scale(cplx<R> *__restrict__ a, uint64_t N,
+                                               const double2 *__restrict__ norm) {
+    const double s = 1.0 / sqrt(norm[0].x);
+    const R sr = R(s);
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += stride) {
+        cplx<R> v = a[i];
+        v.x *= sr;
+        v.y *= sr;
+        a[i] = v;
+    }
+}
+
+template <typename R>
+cudaError_t reduce_t(qs_state *s, int kind, uint64_t a0, uint64_t a1, const void *other) {
+    const cplx<R> *a = static_cast<const cplx<R> *>(s->d);
+    const cplx<R> *b = static_cast<const cplx<R> *>(other);
+    const uint64_t N = uint64_t(1) << s->n;
+    double2 *part = reinterpret_cast<double2 *>(s->partial);
+    double2 *res = reinterpret_cast<double2 *>(s->result);
+    if (kind == RED_PROB_INDEX) {
+        k_prob_index<R><<<1, 1, 0, s->stream>>>(a, a0, res);
+        return cudaGetLastError();
+    }
+    const int quarter = kind == RED_PAULI ? int((a1 >> 62) & 3) : 0;
+    const uint64_t a1m = a1 & ~(uint64_t(3) << 62);
+    switch (kind) {
+    case RED_NORM:
+        k_partial<R, RED_NORM><<<RED_BLOCKS, RED_THREADS, 0, s->stream>>>(a, b, N, a0, a1m, part);
+        break;
+    case RED_PROB_BIT:
+        k_partial<R, RED_PROB_BIT><<<RED_BLOCKS, RED_THREADS, 0, s->stream>>>(a, b, N, a0, a1m, part);
+        break;
+    case RED_PAULI:
+        k_partial<R, RED_PAULI><<<RED_BLOCKS, RED_THREADS, 0, s->stream>>>(a, b, N, a0, a1m, part);
+        break;
+    case RED_INNER:
+        k_partial<R, RED_INNER><<<RED_BLOCKS, RED_THREADS, 0, s->stream>>>(a, b, N, a0, a1m, part);
+        break;
+    default:
+        return cudaErrorInvalidValue;
+    }
+    k_final<<<1, RED_THREADS, 0, s->stream>>>(part, RED_BLOCKS, quarter, res);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// For RED_PAULI: a0 = flip mask, a1 = sign mask with the number of Y factors
+// (mod 4) in its top two bits (n <= 40 leaves them free).
+cudaError_t launch_reduce(qs_state *s, int kind, uint64_t a0, uint64_t a1, const void *other) {
+    return s->dt == QS_C64 ? reduce_t<float>(s, kind, a0, a1, other)
+                           : reduce_t<double>(s, kind, a0, a1, other);
+}
+
+cudaError_t launch_scale(qs_state *s, const double *dev_norm) {
+    const uint64_t N = uint64_t(1) << s->n;
+    uint64_t blocks = (N + 255) / 256;
+    if (blocks > 152ull * 16) blocks = 152ull * 16;
+    const double2 *nr = reinterpret_cast<const double2 *>(dev_norm);
+    if (s->dt == QS_C64)
+        k_scale<float><<<unsigned(blocks), 256, 0, s->stream>>>(static_cast<float2 *>(s->d), N, nr);
+    else
+        k_scale<double><<<unsigned(blocks), 256, 0, s->stream>>>(static_cast<double2 *>(s->d), N, nr);
+    return cudaGetLastError();
+}
+
+}  // namespace qs

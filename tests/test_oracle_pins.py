@@ -16,6 +16,7 @@ import scipy.stats as sst
 
 import oracle
 import workloads as W
+from _util import random_gate, random_state
 
 I2 = np.eye(2, dtype=complex)
 PX = np.array([[0, 1], [1, 0]], dtype=complex)
@@ -91,32 +92,6 @@ def dense_operator(n, g):
         proj[q] = P1 if v else P0
     Pm = kron_list(proj)
     return Pm @ U_big + (id_big - Pm)
-
-
-def random_gate(r, n, allow_swap=True):
-    kinds = ["MATRIX", "H", "X", "Y", "Z", "UP1", "UP2", "UR", "URP1", "RY", "RZ"]
-    if allow_swap and n >= 2:
-        kinds.append("SWAP")
-    kind = kinds[r.integers(len(kinds))]
-    t = int(r.integers(n))
-    t2 = -1
-    busy = {t}
-    if kind == "SWAP":
-        t2 = int(r.choice([q for q in range(n) if q != t]))
-        busy.add(t2)
-    free = [q for q in range(n) if q not in busy]
-    nc = int(r.integers(0, min(3, len(free)) + 1))
-    ctr = {}
-    for q in r.permutation(free)[:nc]:
-        ctr[int(q)] = int(r.integers(2))
-    angles = tuple(float(x) for x in r.uniform(-math.pi, math.pi, size=W.KINDS[kind]))
-    m = W.haar_su2(r) * np.exp(1j * r.uniform(0, 2 * math.pi)) if kind == "MATRIX" else None
-    return W.Gate(kind, t, target2=t2, controls=ctr, angles=angles, matrix=m)
-
-
-def random_state(r, n):
-    v = r.standard_normal(1 << n) + 1j * r.standard_normal(1 << n)
-    return v / np.linalg.norm(v)
 
 
 @pytest.mark.parametrize("kind", ["H", "X", "Y", "Z", "UP1", "UP2", "UR", "URP1", "RY", "RZ", "MATRIX"])
