@@ -51,11 +51,12 @@ def amp_updates(n, gates):
 
 
 def workload_config(args, n_ranks):
+    n = args.n
     return {
         "workload": "random circuit n=%d, %d layers (Haar SU(2) on every qubit + C-NOTs on %d disjoint pairs), %s state"
-                    % (N_QUBITS, LAYERS, N_QUBITS // 2, "complex64" if args.dtype == "c64" else "complex128"),
-        "n_qubits": N_QUBITS, "layers": LAYERS, "gates": LAYERS * (N_QUBITS + N_QUBITS // 2),
-        "state_bytes": (8 if args.dtype == "c64" else 16) << N_QUBITS,
+                    % (n, LAYERS, n // 2, "complex64" if args.dtype == "c64" else "complex128"),
+        "n_qubits": n, "layers": LAYERS, "gates": LAYERS * (n + n // 2),
+        "state_bytes": (8 if args.dtype == "c64" else 16) << n,
         "fused": not args.no_fuse,
         "l2": "state (>= 8 GiB) larger than L2 (129 MB); no flush needed",
         "parallelism": "replicas%d" % n_ranks,
@@ -190,6 +191,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-budget", type=float, default=15.0)
+    ap.add_argument("--n", type=int, default=N_QUBITS,
+                    help="qubits (profiling of smaller cases; the workload is n=30)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -213,7 +216,7 @@ def main():
     from paper_quant_ph_0201042_gb300 import build as qbuild
     qbuild.build()
 
-    n = N_QUBITS
+    n = args.n
     gates = W.random_circuit(n, LAYERS, seed=SEED + rank)
     upd = amp_updates(n, gates)
     plan = qs.Plan(n, args.dtype, gates, fuse=not args.no_fuse)

@@ -181,6 +181,11 @@ qs_status qs_plan_info(const qs_plan *p, int64_t *n_launches, int64_t *n_gates);
 
 qs_status qs_plan_free(qs_plan *p);
 
+/* Writes a human-readable description of the plan (one line per pass: tile
+ * bits, op counts by kind, transposes) into buf (NUL-terminated, truncated to
+ * len bytes).  *needed (may be NULL) receives the full length + 1. */
+qs_status qs_plan_describe(const qs_plan *p, char *buf, size_t len, size_t *needed);
+
 /* Per-launch timing of plan executions, for roofline measurement.  While
  * enabled, qs_plan_execute records a CUDA event pair on the state's stream
  * around every kernel launch it makes; qs_plan_timing waits for the recorded

@@ -79,6 +79,7 @@ _SIGS = {
     "qs_plan_info": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
     "qs_plan_free": [ctypes.c_void_p],
     "qs_plan_set_timing": [ctypes.c_void_p, ctypes.c_int],
+    "qs_plan_describe": [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)],
     "qs_plan_timing": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)],
     "qs_prob": [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)],
     "qs_prob_qubit": [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)],
@@ -293,6 +294,13 @@ class Plan:
     def execute(self, state: State):
         check(lib().qs_plan_execute(state.handle, self._h))
         return state
+
+    def describe(self) -> str:
+        need = ctypes.c_size_t()
+        check(lib().qs_plan_describe(self._h, None, 0, ctypes.byref(need)))
+        buf = ctypes.create_string_buffer(need.value)
+        check(lib().qs_plan_describe(self._h, buf, need.value, None))
+        return buf.value.decode()
 
     def set_timing(self, on: bool = True):
         check(lib().qs_plan_set_timing(self._h, 1 if on else 0))

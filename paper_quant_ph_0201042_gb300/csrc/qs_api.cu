@@ -2,6 +2,7 @@
 // synthesis, state lifetime, and the host side of every call.  All arithmetic
 // on the register runs in the kernels of qs_gates.cu, qs_fused.cu and
 // qs_reduce.cu; nothing here touches amplitudes on the host.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -270,7 +271,8 @@ qs_status qs_apply_swap(qs_state *s, int a, int b) {
     return qs_apply_gate(s, &g);
 }
 
-qs_status qs_plan_create(int n, qs_dtype dt, const qs_gate *g, size_t m, const qs_exec_opts *opts, qs_plan **out) {
+static qs_status plan_create(int n, qs_dtype dt, const qs_gate *g, size_t m, const qs_exec_opts *opts,
+                             qs_plan **out, bool temp) {
     if (!out) return fail(QS_EINVAL, "out is NULL");
     *out = nullptr;
     if (n < 1 || n > QS_MAX_QUBITS) return fail(QS_ERANGE, "n out of range");
@@ -283,10 +285,14 @@ qs_status qs_plan_create(int n, qs_dtype dt, const qs_gate *g, size_t m, const q
     std::memset(&o, 0, sizeof(o));
     if (opts) o = *opts;
     Plan *p = nullptr;
-    st = plan_build(n, dt, ops, o, &p);
+    st = plan_build(n, dt, ops, o, &p, temp);
     if (st != QS_OK) return st;
     *out = reinterpret_cast<qs_plan *>(p);
     return QS_OK;
+}
+
+qs_status qs_plan_create(int n, qs_dtype dt, const qs_gate *g, size_t m, const qs_exec_opts *opts, qs_plan **out) {
+    return plan_create(n, dt, g, m, opts, out, false);
 }
 
 qs_status qs_plan_execute(qs_state *s, const qs_plan *plan) {
@@ -294,6 +300,18 @@ qs_status qs_plan_execute(qs_state *s, const qs_plan *plan) {
     Plan *p = reinterpret_cast<Plan *>(const_cast<qs_plan *>(plan));
     if (plan_n(p) != s->n || plan_dtype(p) != s->dt) return fail(QS_EINVAL, "plan does not match the state");
     return plan_run(s, p);
+}
+
+qs_status qs_plan_describe(const qs_plan *plan, char *buf, size_t len, size_t *needed) {
+    if (!plan) return fail(QS_EINVAL, "plan is NULL");
+    const std::string d = plan_describe(reinterpret_cast<const Plan *>(plan));
+    if (needed) *needed = d.size() + 1;
+    if (buf && len) {
+        const size_t k = std::min(len - 1, d.size());
+        std::memcpy(buf, d.data(), k);
+        buf[k] = 0;
+    }
+    return QS_OK;
 }
 
 qs_status qs_plan_set_timing(qs_plan *plan, int enable) {
@@ -320,10 +338,10 @@ qs_status qs_plan_free(qs_plan *plan) {
 qs_status qs_apply_circuit(qs_state *s, const qs_gate *g, size_t m, const qs_exec_opts *opts) {
     if (!s) return fail(QS_EINVAL, "state is NULL");
     qs_plan *p = nullptr;
-    qs_status st = qs_plan_create(s->n, s->dt, g, m, opts, &p);
+    qs_status st = plan_create(s->n, s->dt, g, m, opts, &p, true);
     if (st != QS_OK) return st;
     st = qs_plan_execute(s, p);
-    qs_plan_free(p);   // launches carry their gate tables by value
+    qs_plan_free(p);   // its gate table is released in stream order
     return st;
 }
 

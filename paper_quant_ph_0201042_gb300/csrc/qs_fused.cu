@@ -29,6 +29,7 @@
 // current pass ahead of a gate that could not, when the two act on disjoint
 // qubits (they commute).
 #include <algorithm>
+#include <cstdio>
 #include <cstring>
 #include <map>
 #include <set>
@@ -40,80 +41,190 @@ namespace qs {
 namespace {
 
 constexpr int LB = 5;          // lane bits
-constexpr int MAX_WB = 3;      // warp bits (8 warps)
-constexpr int MAX_OPS = 120;   // ops per pass (kernel parameter space)
+#ifndef QS_MAX_WB
+#define QS_MAX_WB 3
+#endif
+constexpr int MAX_WB = QS_MAX_WB;  // warp bits (2^MAX_WB warps per CTA)
+constexpr int MAX_OPS = 120;   // ops per pass (shared-memory op table)
+#ifndef QS_RB64
+#define QS_RB64 5
+#endif
+#ifndef QS_WB64
+#define QS_WB64 3
+#endif
+#ifndef QS_RB128
+#define QS_RB128 4
+#endif
+#ifndef QS_FUSED_MINBLOCKS
+#define QS_FUSED_MINBLOCKS 2
+#endif
+constexpr int RB64 = QS_RB64;      // complex64: 2^RB64 amplitudes per thread
+constexpr int WB64 = QS_WB64;      // complex64: 2^WB64 warps per CTA
+constexpr int RB128 = QS_RB128;    // complex128: 2^RB128 amplitudes per thread
+// a layout packs RB + WB slots of 4 bits into 32 bits; a control mask over
+// the register index is 8 bits wide
+static_assert(RB64 + WB64 <= 8 && RB128 + MAX_WB <= 8, "layout does not fit 32 bits");
+static_assert(RB64 <= 5 && RB128 <= 5 && MAX_WB <= 4, "register or warp bits out of range");
 
 enum OpType : uint8_t { OP_REG = 0, OP_LANE = 1, OP_DIAG = 2, OP_XPOSE = 3 };
 
+// Fused-only gate class: an uncontrolled Hadamard applied as the butterfly
+// (x + y, x - y); the factors 1/sqrt 2 of all such gates of a pass are folded
+// into one scale at the store (exact when their number is even, so a complex64
+// register does not drift by the rounding of 1/sqrt 2 once per gate).
+constexpr int GC_HB = 8;
+
 template <typename R>
-struct FOp {
+struct alignas(16) FOp {
     uint8_t type;      // OpType
-    uint8_t cls;       // GateClass (OP_REG / OP_LANE)
+    uint8_t cls;       // GateClass (OP_REG / OP_LANE) or GC_HB
     uint8_t tsel;      // OP_DIAG target: 0 register slot, 1 thread bit, 2 outer bit
     uint8_t tpos;      // register slot / lane bit / thread bit / outer bit
     uint8_t rmask, rval;   // control condition over the register index
-    uint8_t tmask, tval;   // control condition over the thread index (lane | warp << 5)
-    uint8_t lay[8];        // OP_XPOSE: new high-bit index of each register slot, then warp bit
+    uint16_t pad0;
+    uint32_t lay;          // OP_XPOSE: new layout, 4 bits per slot (register slots, then warp bits)
+    uint16_t tmask, tval;  // control condition over the thread index (lane | warp << 5)
     uint64_t omask, oval;  // control condition over the index bits outside the tile
     R u[8];                // matrix, or (d0, d1) for OP_DIAG
 };
 
 template <typename R>
 struct PassDesc {
+    const FOp<R> *ops;     // device op table of this pass
+    uint64_t tiles;        // 2^(n - K)
     int32_t K;             // tile bits
     int32_t WB;            // warp bits
     int32_t nops;
-    int32_t pad;
+    int32_t has_xpose;
+    uint32_t lay0;         // initial layout, 4 bits per slot
+    R scale;               // folded Hadamard factor applied at the store (1: none)
     uint8_t tile_pos[24];  // all tile bit positions, ascending (the first five are 0..4)
     uint8_t hpos[16];      // global position of high tile bit i (= tile_pos[5 + i])
-    uint8_t lay0[8];       // initial layout (register slots, then warp bits)
-    FOp<R> ops[MAX_OPS];
 };
 
-// Global index offset of register index j given the register-slot bit values.
+__device__ __forceinline__ int slot_of(uint32_t lay, int s) { return int((lay >> (4 * s)) & 15u); }
+
+// Global offset of register index j under layout `lay`.
 template <int RB>
-__device__ __forceinline__ uint64_t reg_offset(int j, const uint64_t (&rpos)[RB]) {
+__device__ __forceinline__ uint64_t reg_offset(int j, uint32_t lay, const uint8_t *hpos) {
     uint64_t o = 0;
 #pragma unroll
     for (int r = 0; r < RB; ++r)
-        if ((j >> r) & 1) o |= rpos[r];
+        if ((j >> r) & 1) o |= uint64_t(1) << hpos[slot_of(lay, r)];
     return o;
 }
 
+// Global offset of this thread's lane and warp bits under layout `lay`.
 template <int RB>
-__device__ __forceinline__ uint32_t reg_local(int j, const uint32_t (&lpos)[RB]) {
-    uint32_t o = 0;
+__device__ __forceinline__ uint64_t thread_offset(uint32_t lane, uint32_t warp, int WB, uint32_t lay,
+                                                  const uint8_t *hpos) {
+    uint64_t o = lane;
+#pragma unroll
+    for (int w = 0; w < MAX_WB; ++w)
+        if (w < WB && ((warp >> w) & 1)) o |= uint64_t(1) << hpos[slot_of(lay, RB + w)];
+    return o;
+}
+
+// Tile-local (shared memory) index of register index j of this thread.
+template <int RB>
+__device__ __forceinline__ uint32_t local_index(int j, uint32_t lane, uint32_t warp, int WB, uint32_t lay) {
+    uint32_t o = lane;
 #pragma unroll
     for (int r = 0; r < RB; ++r)
-        if ((j >> r) & 1) o |= lpos[r];
+        if ((j >> r) & 1) o |= 1u << (LB + slot_of(lay, r));
+#pragma unroll
+    for (int w = 0; w < MAX_WB; ++w)
+        if (w < WB && ((warp >> w) & 1)) o |= 1u << (LB + slot_of(lay, RB + w));
     return o;
 }
 
-template <typename R, int RB, int T>
-__device__ __forceinline__ void apply_reg(cplx<R> (&v)[1 << RB], const FOp<R> &op, bool ok) {
-    const cplx<R> u00 = mk<R>(op.u[0], op.u[1]), u01 = mk<R>(op.u[2], op.u[3]);
-    const cplx<R> u10 = mk<R>(op.u[4], op.u[5]), u11 = mk<R>(op.u[6], op.u[7]);
-    const int cls = op.cls;
-    const int rm = op.rmask, rv = op.rval;
+// Matrix of an op, read from shared memory with vector loads.
+template <typename R> struct Mat4 { cplx<R> u00, u01, u10, u11; };
+
+__device__ __forceinline__ Mat4<double> load_mat(const FOp<double> &op) {
+    const double2 *p = reinterpret_cast<const double2 *>(&op.u[0]);
+    return {p[0], p[1], p[2], p[3]};
+}
+
+template <typename R>
+__device__ __forceinline__ cplx<R> sel(bool p, cplx<R> a, cplx<R> b) { return mk<R>(p ? a.x : b.x, p ? a.y : b.y); }
+
+// General 2x2 on register slot T.  With PRED, pairs whose register bits fail
+// the control condition keep their values (select, no branch); without, every
+// pair is updated (the common case: no control on a register bit).
+template <typename R, int RB, int T, bool PRED>
+__device__ __forceinline__ void reg_gen(cplx<R> (&v)[1 << RB], const Mat4<R> &m, int rm, int rv) {
 #pragma unroll
     for (int j = 0; j < (1 << RB); ++j) {
         if ((j >> T) & 1) continue;
         const int j1 = j | (1 << T);
-        if (!(ok && ((j & rm) == rv))) continue;
         const cplx<R> x = v[j], y = v[j1];
-        if (cls == GC_GEN) {
-            v[j] = cmad2<R>(u00, x, u01, y);
-            v[j1] = cmad2<R>(u10, x, u11, y);
-        } else if (cls == GC_REAL) {
-            v[j] = rmad2<R>(u00.x, x, u01.x, y);
-            v[j1] = rmad2<R>(u10.x, x, u11.x, y);
-        } else if (cls == GC_ANTI) {
-            v[j] = cmul<R>(u01, y);
-            v[j1] = cmul<R>(u10, x);
-        } else {  // GC_X
+        if (PRED) {
+            const bool p = (j & rm) == rv;
+            v[j] = sel<R>(p, cmad2<R>(m.u00, x, m.u01, y), x);
+            v[j1] = sel<R>(p, cmad2<R>(m.u10, x, m.u11, y), y);
+        } else {
+            v[j] = cmad2<R>(m.u00, x, m.u01, y);
+            v[j1] = cmad2<R>(m.u10, x, m.u11, y);
+        }
+    }
+}
+
+// Exchange of the pair (X, C-NOT) on register slot T; without PRED it is a
+// renaming of registers.
+template <typename R, int RB, int T, bool PRED>
+__device__ __forceinline__ void reg_x(cplx<R> (&v)[1 << RB], int rm, int rv) {
+#pragma unroll
+    for (int j = 0; j < (1 << RB); ++j) {
+        if ((j >> T) & 1) continue;
+        const int j1 = j | (1 << T);
+        const cplx<R> x = v[j], y = v[j1];
+        if (PRED) {
+            const bool p = (j & rm) == rv;
+            v[j] = sel<R>(p, y, x);
+            v[j1] = sel<R>(p, x, y);
+        } else {
             v[j] = y;
             v[j1] = x;
         }
+    }
+}
+
+// Uncontrolled Hadamard butterfly on register slot T (scale folded).
+template <typename R, int RB, int T>
+__device__ __forceinline__ void reg_hb(cplx<R> (&v)[1 << RB]) {
+#pragma unroll
+    for (int j = 0; j < (1 << RB); ++j) {
+        if ((j >> T) & 1) continue;
+        const int j1 = j | (1 << T);
+        const cplx<R> x = v[j], y = v[j1];
+        v[j] = mk<R>(x.x + y.x, x.y + y.y);
+        v[j1] = mk<R>(x.x - y.x, x.y - y.y);
+    }
+}
+
+// Diagonal gate whose target is register slot T: d0 on amplitudes with bit T
+// clear, d1 on those with it set; DK = 1: d0 == 1 (skip), DK = 2: d1 == 1.
+template <typename R, int RB, int T>
+__device__ __forceinline__ void reg_diag(cplx<R> (&v)[1 << RB], int dk, cplx<R> d0, cplx<R> d1, int rm, int rv) {
+#pragma unroll
+    for (int j = 0; j < (1 << RB); ++j) {
+        const bool hi = (j >> T) & 1;
+        if ((hi && dk == 2) || (!hi && dk == 1)) continue;
+        v[j] = sel<R>((j & rm) == rv, cmul<R>(hi ? d1 : d0, v[j]), v[j]);
+    }
+}
+
+template <typename R, int RB, int T>
+__device__ __forceinline__ void reg_op(cplx<R> (&v)[1 << RB], int cls, int rm, int rv, const FOp<R> &op) {
+    if (cls == GC_HB) reg_hb<R, RB, T>(v);
+    else if (cls == GC_X) {
+        if (rm) reg_x<R, RB, T, true>(v, rm, rv);
+        else reg_x<R, RB, T, false>(v, rm, rv);
+    } else {
+        const Mat4<R> m = load_mat(op);
+        if (rm) reg_gen<R, RB, T, true>(v, m, rm, rv);
+        else reg_gen<R, RB, T, false>(v, m, rm, rv);
     }
 }
 
@@ -122,126 +233,420 @@ __device__ __forceinline__ cplx<R> shfl(cplx<R> a, int m) {
     return mk<R>(__shfl_xor_sync(0xffffffffu, a.x, m), __shfl_xor_sync(0xffffffffu, a.y, m));
 }
 
+// One CTA runs tiles blockIdx.x, blockIdx.x + gridDim.x, ... (persistent).
+// Shared memory: the transpose buffer (2^K amplitudes, only when the pass
+// transposes), then the op table of the pass.
 template <typename R, int RB>
-__global__ void __launch_bounds__(256) k_fused(cplx<R> *__restrict__ a, const __grid_constant__ PassDesc<R> P) {
+__global__ void __launch_bounds__(32 << QS_MAX_WB, 1) k_fused(cplx<R> *__restrict__ a, const __grid_constant__ PassDesc<R> P) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    cplx<R> *sm = reinterpret_cast<cplx<R> *>(smraw);
     constexpr int NA = 1 << RB;
-    const int K = P.K, WB = P.WB;
+    const int K = P.K, WB = P.WB, nops = P.nops;
+    cplx<R> *sm = reinterpret_cast<cplx<R> *>(smraw);
+    FOp<R> *sops = reinterpret_cast<FOp<R> *>(smraw + (P.has_xpose ? (size_t(sizeof(cplx<R>)) << K) : 0));
+    {
+        const uint4 *src = reinterpret_cast<const uint4 *>(P.ops);
+        uint4 *dst = reinterpret_cast<uint4 *>(sops);
+        const int words = nops * int(sizeof(FOp<R>) / 16);
+        for (int k = threadIdx.x; k < words; k += blockDim.x) dst[k] = src[k];
+        __syncthreads();
+    }
     const uint32_t tl = threadIdx.x;            // lane | warp << 5
     const uint32_t lane = tl & 31u, warp = tl >> 5;
 
-    // tile base: the block index with zeros inserted at every tile position
-    uint64_t base = blockIdx.x;
-    for (int k = 0; k < K; ++k) {
-        const uint64_t low = (uint64_t(1) << P.tile_pos[k]) - 1;
-        base = ((base & ~low) << 1) | (base & low);
-    }
-
-    // layout: high-bit index of each register slot and warp bit
-    int rh[RB], wh[MAX_WB];
-#pragma unroll
-    for (int r = 0; r < RB; ++r) rh[r] = P.lay0[r];
-#pragma unroll
-    for (int w = 0; w < MAX_WB; ++w) wh[w] = w < WB ? P.lay0[RB + w] : 0;
-
-    uint64_t rpos[RB];
-    uint64_t toff = lane;
-#pragma unroll
-    for (int r = 0; r < RB; ++r) rpos[r] = uint64_t(1) << P.hpos[rh[r]];
-#pragma unroll
-    for (int w = 0; w < MAX_WB; ++w)
-        if (w < WB && ((warp >> w) & 1)) toff |= uint64_t(1) << P.hpos[wh[w]];
-
-    cplx<R> v[NA];
-    const cplx<R> *src = a + (base | toff);
-#pragma unroll
-    for (int j = 0; j < NA; ++j) v[j] = src[reg_offset<RB>(j, rpos)];
-
-    for (int k = 0; k < P.nops; ++k) {
-        const FOp<R> &op = P.ops[k];
-        const int type = op.type;
-        if (type == OP_XPOSE) {
-            // write with the current layout, read back with the new one
-            uint32_t lpos[RB];
-            uint32_t tloc = lane;
-#pragma unroll
-            for (int r = 0; r < RB; ++r) lpos[r] = 1u << (LB + rh[r]);
-#pragma unroll
-            for (int w = 0; w < MAX_WB; ++w)
-                if (w < WB && ((warp >> w) & 1)) tloc |= 1u << (LB + wh[w]);
-#pragma unroll
-            for (int j = 0; j < NA; ++j) sm[tloc | reg_local<RB>(j, lpos)] = v[j];
-            __syncthreads();
-#pragma unroll
-            for (int r = 0; r < RB; ++r) rh[r] = op.lay[r];
-#pragma unroll
-            for (int w = 0; w < MAX_WB; ++w) wh[w] = w < WB ? op.lay[RB + w] : 0;
-            tloc = lane;
-#pragma unroll
-            for (int r = 0; r < RB; ++r) lpos[r] = 1u << (LB + rh[r]);
-#pragma unroll
-            for (int w = 0; w < MAX_WB; ++w)
-                if (w < WB && ((warp >> w) & 1)) tloc |= 1u << (LB + wh[w]);
-#pragma unroll
-            for (int j = 0; j < NA; ++j) v[j] = sm[tloc | reg_local<RB>(j, lpos)];
-            __syncthreads();
-            continue;
+    for (uint64_t tile = blockIdx.x; tile < P.tiles; tile += gridDim.x) {
+        // tile base: the tile index with zeros inserted at every tile position
+        uint64_t base = tile;
+        for (int k = 0; k < K; ++k) {
+            const uint64_t low = (uint64_t(1) << P.tile_pos[k]) - 1;
+            base = ((base & ~low) << 1) | (base & low);
         }
-        const bool ok = ((tl & op.tmask) == op.tval) && ((base & op.omask) == op.oval);
-        if (type == OP_REG) {
-            switch (op.tpos) {
-            case 0: apply_reg<R, RB, 0>(v, op, ok); break;
-            case 1: apply_reg<R, RB, 1>(v, op, ok); break;
-            case 2: apply_reg<R, RB, 2>(v, op, ok); break;
-            case 3: apply_reg<R, RB, 3>(v, op, ok); break;
-            default: if (RB > 4) apply_reg<R, RB, (RB > 4 ? 4 : 0)>(v, op, ok); break;
-            }
-        } else if (type == OP_LANE) {
-            const int m = 1 << op.tpos;
-            const bool hi = (lane >> op.tpos) & 1;
-            const cplx<R> u00 = mk<R>(op.u[0], op.u[1]), u01 = mk<R>(op.u[2], op.u[3]);
-            const cplx<R> u10 = mk<R>(op.u[4], op.u[5]), u11 = mk<R>(op.u[6], op.u[7]);
-            // the coefficient on my own amplitude and on the partner's
-            const cplx<R> cs = hi ? u11 : u00, co = hi ? u10 : u01;
-            const int cls = op.cls;
+        uint32_t lay = P.lay0;
+        cplx<R> v[NA];
+        {
+            const cplx<R> *src = a + (base | thread_offset<RB>(lane, warp, WB, lay, P.hpos));
 #pragma unroll
-            for (int j = 0; j < NA; ++j) {
-                if ((j & op.rmask) != op.rval) continue;   // uniform across the warp
-                const cplx<R> o = shfl<R>(v[j], m);
+            for (int j = 0; j < NA; ++j) v[j] = src[reg_offset<RB>(j, lay, P.hpos)];
+        }
+        for (int k = 0; k < nops; ++k) {
+            const FOp<R> &op = sops[k];
+            const uint4 hd = *reinterpret_cast<const uint4 *>(&op);
+            const int type = hd.x & 0xff, cls = (hd.x >> 8) & 0xff, tsel = (hd.x >> 16) & 0xff,
+                      tpos = hd.x >> 24;
+            const int rm = hd.y & 0xff, rv = (hd.y >> 8) & 0xff;
+            const uint32_t tm = hd.w & 0xffff, tv = hd.w >> 16;
+            if (type == OP_XPOSE) {
+                // write with the current layout, read back with the new one
+#pragma unroll
+                for (int j = 0; j < NA; ++j) sm[local_index<RB>(j, lane, warp, WB, lay)] = v[j];
+                __syncthreads();
+                lay = hd.z;
+#pragma unroll
+                for (int j = 0; j < NA; ++j) v[j] = sm[local_index<RB>(j, lane, warp, WB, lay)];
+                __syncthreads();
+                continue;
+            }
+            const bool ok = ((tl & tm) == tv) && ((base & op.omask) == op.oval);
+            if (type == OP_REG) {
                 if (!ok) continue;
-                if (cls == GC_GEN) v[j] = cmad2<R>(cs, v[j], co, o);
-                else if (cls == GC_REAL) v[j] = rmad2<R>(cs.x, v[j], co.x, o);
-                else if (cls == GC_ANTI) v[j] = cmul<R>(co, o);
-                else v[j] = o;
-            }
-        } else {  // OP_DIAG
-            const cplx<R> d0 = mk<R>(op.u[0], op.u[1]), d1 = mk<R>(op.u[2], op.u[3]);
-            if (op.tsel == 0) {
+                if (tpos == 0) reg_op<R, RB, 0>(v, cls, rm, rv, op);
+                else if (tpos == 1) reg_op<R, RB, 1>(v, cls, rm, rv, op);
+                else if (tpos == 2) reg_op<R, RB, 2>(v, cls, rm, rv, op);
+                else if (tpos == 3) reg_op<R, RB, 3>(v, cls, rm, rv, op);
+                else reg_op<R, RB, (RB > 4 ? 4 : 0)>(v, cls, rm, rv, op);
+            } else if (type == OP_LANE) {
+                // partners sit in the lane that differs in bit tpos; both lanes
+                // exchange their old values before either writes
+                const int m = 1 << tpos;
+                const bool hi = (lane >> tpos) & 1;
+                if (cls == GC_HB) {
 #pragma unroll
-                for (int j = 0; j < NA; ++j)
-                    if (ok && ((j & op.rmask) == op.rval)) v[j] = cmul<R>(((j >> op.tpos) & 1) ? d1 : d0, v[j]);
-            } else {
-                const uint64_t word = op.tsel == 1 ? uint64_t(tl) : base;
-                const cplx<R> d = ((word >> op.tpos) & 1) ? d1 : d0;
+                    for (int j = 0; j < NA; ++j) {
+                        const cplx<R> o = shfl<R>(v[j], m);
+                        v[j] = hi ? mk<R>(o.x - v[j].x, o.y - v[j].y) : mk<R>(v[j].x + o.x, v[j].y + o.y);
+                    }
+                } else if (cls == GC_X) {
+                    if (rm == 0) {
 #pragma unroll
-                for (int j = 0; j < NA; ++j)
-                    if (ok && ((j & op.rmask) == op.rval)) v[j] = cmul<R>(d, v[j]);
+                        for (int j = 0; j < NA; ++j) {
+                            const cplx<R> o = shfl<R>(v[j], m);
+                            v[j] = sel<R>(ok, o, v[j]);
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < NA; ++j) {
+                            if ((j & rm) != rv) continue;   // uniform across the warp
+                            const cplx<R> o = shfl<R>(v[j], m);
+                            v[j] = sel<R>(ok, o, v[j]);
+                        }
+                    }
+                } else {
+                    const Mat4<R> mt = load_mat(op);
+                    // coefficients on my own amplitude and on the partner's
+                    const cplx<R> cs = hi ? mt.u11 : mt.u00, co = hi ? mt.u10 : mt.u01;
+                    if (rm == 0 && __all_sync(0xffffffffu, ok)) {
+#pragma unroll
+                        for (int j = 0; j < NA; ++j) {
+                            const cplx<R> o = shfl<R>(v[j], m);
+                            v[j] = cmad2<R>(cs, v[j], co, o);
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < NA; ++j) {
+                            if ((j & rm) != rv) continue;   // uniform across the warp
+                            const cplx<R> o = shfl<R>(v[j], m);
+                            v[j] = sel<R>(ok, cmad2<R>(cs, v[j], co, o), v[j]);
+                        }
+                    }
+                }
+            } else {  // OP_DIAG
+                if (!ok) continue;
+                const Mat4<R> mt = load_mat(op);   // (d0, d1) in the first two entries
+                const cplx<R> d0 = mt.u00, d1 = mt.u01;
+                if (tsel == 0) {
+                    if (tpos == 0) reg_diag<R, RB, 0>(v, cls, d0, d1, rm, rv);
+                    else if (tpos == 1) reg_diag<R, RB, 1>(v, cls, d0, d1, rm, rv);
+                    else if (tpos == 2) reg_diag<R, RB, 2>(v, cls, d0, d1, rm, rv);
+                    else if (tpos == 3) reg_diag<R, RB, 3>(v, cls, d0, d1, rm, rv);
+                    else reg_diag<R, RB, (RB > 4 ? 4 : 0)>(v, cls, d0, d1, rm, rv);
+                } else {
+                    const uint64_t word = tsel == 1 ? uint64_t(tl) : base;
+                    const cplx<R> d = ((word >> tpos) & 1) ? d1 : d0;
+#pragma unroll
+                    for (int j = 0; j < NA; ++j) v[j] = sel<R>((j & rm) == rv, cmul<R>(d, v[j]), v[j]);
+                }
             }
         }
+        if (P.scale != R(1)) {
+#pragma unroll
+            for (int j = 0; j < NA; ++j) v[j] = mk<R>(v[j].x * P.scale, v[j].y * P.scale);
+        }
+        // store with the final layout
+        cplx<R> *dst = a + (base | thread_offset<RB>(lane, warp, WB, lay, P.hpos));
+#pragma unroll
+        for (int j = 0; j < NA; ++j) dst[reg_offset<RB>(j, lay, P.hpos)] = v[j];
     }
-
-    // store with the final layout
-#pragma unroll
-    for (int r = 0; r < RB; ++r) rpos[r] = uint64_t(1) << P.hpos[rh[r]];
-    toff = lane;
-#pragma unroll
-    for (int w = 0; w < MAX_WB; ++w)
-        if (w < WB && ((warp >> w) & 1)) toff |= uint64_t(1) << P.hpos[wh[w]];
-    cplx<R> *dst = a + (base | toff);
-#pragma unroll
-    for (int j = 0; j < NA; ++j) dst[reg_offset<RB>(j, rpos)] = v[j];
 }
+
+// ---------------------------------------------------------------------------
+// Complex64 pass kernel.
+//
+// Each thread keeps 32 amplitudes (register index j, 5 register bits) as
+// (re, im) pairs and updates them with scalar FFMA (packing two amplitudes
+// per FFMA2 costs more in register moves than it saves in issue slots).
+//
+// Exchanges (X, C-NOT) on a register slot whose condition is uniform across
+// the warp move no data: each thread keeps a mask xm such that physical
+// register index p holds the amplitude of logical register index p ^ xm.
+// Later gates read their matrix in swapped roles (X U X) where xm has their
+// slot, control predicates and diagonal selectors use the logical index
+// p ^ xm, and transposes and the store put physical p at the place of p ^ xm.
+//
+// Every layout-dependent offset (global offsets of register indices and warp
+// bits at the load and at the store, the read pattern of each transpose) is
+// computed on the host when the plan is built, so the kernel does no bit
+// scattering.
+// ---------------------------------------------------------------------------
+
+// One op of the complex64 kernel (112 bytes).
+struct alignas(16) POp {
+    uint8_t type, cls, tsel, tpos;
+    uint8_t rmask, rval;
+    uint16_t pad0;
+    uint32_t pad1;
+    uint16_t tmask, tval;
+    uint64_t omask, oval;
+    // OP_REG / OP_LANE: u00, u01, u10, u11 in c[0..3]; OP_DIAG: d0, d1 in c[0..1]
+    // OP_XPOSE: 32 uint16 read offsets (old tile order) of the new register
+    //           indices in c[0..7], then the old tile-order bit of each new
+    //           warp bit (bytes) in c[8..9]
+    float2 c[10];
+};
+static_assert(sizeof(POp) == 112, "POp layout");
+
+struct PassC64 {
+    const POp *ops;
+    uint64_t tiles;
+    int32_t K, WB, nops, has_xpose;
+    float scale;
+    int32_t pad;
+    uint8_t tile_pos[24];
+    uint64_t ld_reg[32], ld_warp[4];   // global offsets of register index j / warp bit w (first layout)
+    uint64_t st_reg[32], st_warp[4];   // the same for the last layout (store)
+};
+
+__device__ __forceinline__ bool lpred(int j, uint32_t xm, int rm, int rv) {
+    return ((uint32_t(j) ^ xm) & uint32_t(rm)) == uint32_t(rv);
+}
+
+template <int T, bool PRED, int NA>
+__device__ __forceinline__ void s_gen(float2 (&v)[NA], Mat4<float> m, uint32_t xm, int rm, int rv) {
+    if ((xm >> T) & 1) {
+        float2 t = m.u00; m.u00 = m.u11; m.u11 = t;
+        t = m.u01; m.u01 = m.u10; m.u10 = t;
+    }
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+        if ((j >> T) & 1) continue;
+        const int j1 = j | (1 << T);
+        const float2 x = v[j], y = v[j1];
+        const float2 nx = cmad2<float>(m.u00, x, m.u01, y), ny = cmad2<float>(m.u10, x, m.u11, y);
+        if (PRED) {
+            const bool p = lpred(j, xm, rm, rv);
+            v[j] = p ? nx : x;
+            v[j1] = p ? ny : y;
+        } else {
+            v[j] = nx;
+            v[j1] = ny;
+        }
+    }
+}
+
+template <int T, int NA>
+__device__ __forceinline__ void s_xdata(float2 (&v)[NA], uint32_t xm, int rm, int rv, bool ok) {
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+        if ((j >> T) & 1) continue;
+        const int j1 = j | (1 << T);
+        const bool p = ok && lpred(j, xm, rm, rv);
+        const float2 x = v[j], y = v[j1];
+        v[j] = p ? y : x;
+        v[j1] = p ? x : y;
+    }
+}
+
+template <int T, int NA>
+__device__ __forceinline__ void s_hb(float2 (&v)[NA], uint32_t xm) {
+    const bool sw = (xm >> T) & 1;
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+        if ((j >> T) & 1) continue;
+        const int j1 = j | (1 << T);
+        const float2 x = v[j], y = v[j1];
+        const float2 sm = make_float2(x.x + y.x, x.y + y.y), df = make_float2(x.x - y.x, x.y - y.y);
+        v[j] = sw ? make_float2(-df.x, -df.y) : sm;
+        v[j1] = sw ? sm : df;
+    }
+}
+
+template <int T, int NA>
+__device__ __forceinline__ void s_diag(float2 (&v)[NA], float2 d0, float2 d1, uint32_t xm, int rm, int rv) {
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+        const uint32_t l = uint32_t(j) ^ xm;
+        const float2 d = ((l >> T) & 1) ? d1 : d0;
+        if ((l & uint32_t(rm)) == uint32_t(rv)) v[j] = cmul<float>(d, v[j]);
+    }
+}
+
+template <int T, int NA>
+__device__ __forceinline__ void s_reg_op(float2 (&v)[NA], int cls, uint32_t &xm, bool ok, int rm, int rv, bool lanectl,
+                                         const Mat4<float> &m) {
+    if (cls == GC_X) {
+        if (rm == 0 && !lanectl) { xm ^= ok ? (1u << T) : 0u; return; }
+        s_xdata<T, NA>(v, xm, rm, rv, ok);
+        return;
+    }
+    if (!ok) return;
+    if (cls == GC_HB) { s_hb<T, NA>(v, xm); return; }
+    if (rm) s_gen<T, true, NA>(v, m, xm, rm, rv);
+    else s_gen<T, false, NA>(v, m, xm, rm, rv);
+}
+
+__global__ void __launch_bounds__(32 << QS_WB64, QS_FUSED_MINBLOCKS) k_fused_c64(float2 *__restrict__ a,
+                                                                       const __grid_constant__ PassC64 P) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int K = P.K, WB = P.WB, nops = P.nops;
+    float2 *sm = reinterpret_cast<float2 *>(smraw);
+    POp *sops = reinterpret_cast<POp *>(smraw + (P.has_xpose ? (size_t(8) << K) : 0));
+    {
+        const uint4 *src = reinterpret_cast<const uint4 *>(P.ops);
+        uint4 *dst = reinterpret_cast<uint4 *>(sops);
+        const int words = nops * int(sizeof(POp) / 16);
+        for (int k = threadIdx.x; k < words; k += blockDim.x) dst[k] = src[k];
+        __syncthreads();
+    }
+    const uint32_t tl = threadIdx.x;
+    const uint32_t lane = tl & 31u, warp = tl >> 5;
+    const int stride = 32 << WB;
+    uint64_t ld_t = lane, st_t = lane;
+#pragma unroll
+    for (int w = 0; w < WB64; ++w)
+        if ((warp >> w) & 1) { ld_t += P.ld_warp[w]; st_t += P.st_warp[w]; }
+
+    for (uint64_t tile = blockIdx.x; tile < P.tiles; tile += gridDim.x) {
+        uint64_t base = tile;
+        for (int k = 0; k < K; ++k) {
+            const uint64_t low = (uint64_t(1) << P.tile_pos[k]) - 1;
+            base = ((base & ~low) << 1) | (base & low);
+        }
+        uint32_t xm = 0;
+        constexpr int NA = 1 << RB64;
+        float2 v[NA];
+        {
+            const float2 *src = a + (base | ld_t);
+#pragma unroll
+            for (int j = 0; j < NA; ++j) v[j] = src[P.ld_reg[j]];
+        }
+        for (int k = 0; k < nops; ++k) {
+            const POp &op = sops[k];
+            const uint4 *q = reinterpret_cast<const uint4 *>(&op);
+            const uint4 hd = q[0], oc = q[1];
+            const int type = hd.x & 0xff, cls = (hd.x >> 8) & 0xff, tsel = (hd.x >> 16) & 0xff,
+                      tpos = hd.x >> 24;
+            const int rm = hd.y & 0xff, rv = (hd.y >> 8) & 0xff;
+            const uint32_t tm = hd.w & 0xffff, tv = hd.w >> 16;
+            if (type == OP_XPOSE) {
+                const uint32_t cw = (xm * uint32_t(stride)) | tl;
+#pragma unroll
+                for (int j = 0; j < NA; ++j) sm[uint32_t(j * stride) ^ cw] = v[j];
+                const uint4 *rt = reinterpret_cast<const uint4 *>(op.c);
+                uint32_t rd[16];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const uint4 w4 = rt[q];
+                    rd[4 * q] = w4.x; rd[4 * q + 1] = w4.y; rd[4 * q + 2] = w4.z; rd[4 * q + 3] = w4.w;
+                }
+                const uint4 ow4 = rt[4];
+                uint32_t cth = lane;
+#pragma unroll
+                for (int w = 0; w < WB64; ++w)
+                    if (w < WB && ((warp >> w) & 1)) cth |= 1u << ((ow4.x >> (8 * w)) & 0xff);
+                __syncthreads();
+                xm = 0;
+#pragma unroll
+                for (int j = 0; j < NA; ++j) v[j] = sm[((rd[j >> 1] >> (16 * (j & 1))) & 0xffff) ^ cth];
+                __syncthreads();
+                continue;
+            }
+            const uint64_t omask = uint64_t(oc.x) | (uint64_t(oc.y) << 32);
+            const uint64_t oval = uint64_t(oc.z) | (uint64_t(oc.w) << 32);
+            const bool ok = ((tl & tm) == tv) && ((base & omask) == oval);
+            const float4 c0 = reinterpret_cast<const float4 *>(q)[2], c1 = reinterpret_cast<const float4 *>(q)[3];
+            const Mat4<float> mt = {make_float2(c0.x, c0.y), make_float2(c0.z, c0.w), make_float2(c1.x, c1.y),
+                                    make_float2(c1.z, c1.w)};
+            if (type == OP_REG) {
+                const bool lc = (tm & 31u) != 0;
+                if (tpos == 0) s_reg_op<0, NA>(v, cls, xm, ok, rm, rv, lc, mt);
+                else if (tpos == 1) s_reg_op<1, NA>(v, cls, xm, ok, rm, rv, lc, mt);
+                else if (tpos == 2) s_reg_op<2, NA>(v, cls, xm, ok, rm, rv, lc, mt);
+                else if (tpos == 3) s_reg_op<3, NA>(v, cls, xm, ok, rm, rv, lc, mt);
+                else s_reg_op<(RB64 > 4 ? 4 : 0), NA>(v, cls, xm, ok, rm, rv, lc, mt);
+            } else if (type == OP_LANE) {
+                const int m = 1 << tpos;
+                const bool hi = (lane >> tpos) & 1;
+                if (cls == GC_HB) {
+#pragma unroll
+                    for (int j = 0; j < NA; ++j) {
+                        const float2 o = shfl<float>(v[j], m);
+                        v[j] = hi ? make_float2(o.x - v[j].x, o.y - v[j].y) : make_float2(v[j].x + o.x, v[j].y + o.y);
+                    }
+                } else if (cls == GC_X) {
+#pragma unroll
+                    for (int j = 0; j < NA; ++j) {
+                        const float2 o = shfl<float>(v[j], m);
+                        if (ok && lpred(j, xm, rm, rv)) v[j] = o;
+                    }
+                } else {
+                    const float2 cs = hi ? mt.u11 : mt.u00, co = hi ? mt.u10 : mt.u01;
+                    if (rm == 0 && __all_sync(0xffffffffu, ok)) {
+#pragma unroll
+                        for (int j = 0; j < NA; ++j) {
+                            const float2 o = shfl<float>(v[j], m);
+                            v[j] = cmad2<float>(cs, v[j], co, o);
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < NA; ++j) {
+                            const float2 o = shfl<float>(v[j], m);
+                            if (ok && lpred(j, xm, rm, rv)) v[j] = cmad2<float>(cs, v[j], co, o);
+                        }
+                    }
+                }
+            } else {  // OP_DIAG
+                if (!ok) continue;
+                const float2 d0 = mt.u00, d1 = mt.u01;
+                if (tsel == 0) {
+                    if (tpos == 0) s_diag<0, NA>(v, d0, d1, xm, rm, rv);
+                    else if (tpos == 1) s_diag<1, NA>(v, d0, d1, xm, rm, rv);
+                    else if (tpos == 2) s_diag<2, NA>(v, d0, d1, xm, rm, rv);
+                    else if (tpos == 3) s_diag<3, NA>(v, d0, d1, xm, rm, rv);
+                    else s_diag<(RB64 > 4 ? 4 : 0), NA>(v, d0, d1, xm, rm, rv);
+                } else {
+                    const uint64_t word = tsel == 1 ? uint64_t(tl) : base;
+                    const float2 d = ((word >> tpos) & 1) ? d1 : d0;
+#pragma unroll
+                    for (int j = 0; j < NA; ++j)
+                        if (lpred(j, xm, rm, rv)) v[j] = cmul<float>(d, v[j]);
+                }
+            }
+        }
+        if (P.scale != 1.f) {
+#pragma unroll
+            for (int j = 0; j < NA; ++j) v[j] = make_float2(v[j].x * P.scale, v[j].y * P.scale);
+        }
+        float2 *dst = a + (base | st_t);
+        if (xm == 0) {
+#pragma unroll
+            for (int j = 0; j < NA; ++j) dst[P.st_reg[j]] = v[j];
+        } else {
+            uint64_t xg = 0;
+#pragma unroll
+            for (int r = 0; r < RB64; ++r)
+                if ((xm >> r) & 1) xg |= P.st_reg[1 << r];
+#pragma unroll
+            for (int j = 0; j < NA; ++j) dst[P.st_reg[j] ^ xg] = v[j];
+        }
+    }
+}
+
+// The pass kernel of each precision.
+template <typename R, int RB> struct PassKernel;
+template <> struct PassKernel<double, RB128> {
+    static void *ptr() { return reinterpret_cast<void *>(&k_fused<double, RB128>); }
+    static void launch(unsigned g, unsigned b, size_t sm, cudaStream_t st, double2 *a, const PassDesc<double> &D) {
+        k_fused<double, RB128><<<g, b, sm, st>>>(a, D);
+    }
+};
 
 // ---------------------------------------------------------------------------
 // Host planner
@@ -289,8 +694,16 @@ struct Plan {
     std::vector<HostOp> ops;                 // unfused mode
     std::vector<PassDesc<float>> pf;         // fused passes, complex64
     std::vector<PassDesc<double>> pd;        // fused passes, complex128
+    std::vector<std::vector<FOp<float>>> of; // op tables of the passes (host)
+    std::vector<PassC64> pc;                 // complex64 kernel descriptors
+    std::vector<std::vector<POp>> pco;       // complex64 kernel op tables (host)
+    std::vector<std::vector<FOp<double>>> od;
+    void *dev_ops = nullptr;                 // all op tables (device), owned
+    bool temp = false;                       // stream-ordered table (one-shot plan)
+    cudaStream_t free_stream = nullptr;
     int64_t n_gates = 0;
     int RB = 0;
+    int grid = 0;                            // persistent grid size
     // per-launch timing (qs_plan_set_timing)
     bool timing = false;
     std::vector<cudaEvent_t> ev;             // begin/end pairs
@@ -298,6 +711,10 @@ struct Plan {
 
     ~Plan() {
         for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        if (dev_ops) {
+            if (temp) cudaFreeAsync(dev_ops, free_stream);
+            else cudaFree(dev_ops);
+        }
     }
     // records the begin (end = false) or end event of a launch
     cudaError_t mark(cudaStream_t st, bool end) {
@@ -315,8 +732,17 @@ struct Plan {
 
 namespace {
 
+uint32_t pack_layout(const std::vector<int> &regs, const std::vector<int> &warps) {
+    uint32_t lay = 0;
+    int s = 0;
+    for (int r : regs) lay |= uint32_t(r) << (4 * s++);
+    for (int w : warps) lay |= uint32_t(w) << (4 * s++);
+    return lay;
+}
+
 template <typename R>
-qs_status resolve_pass(int n, int RB, int WB, const PlannedPass &pp, PassDesc<R> &D) {
+qs_status resolve_pass(int n, int RB, int WB, const PlannedPass &pp, PassDesc<R> &D,
+                       std::vector<FOp<R>> &ops_out) {
     const int H = RB + WB;
     std::memset(&D, 0, sizeof(D));
     D.K = LB + H;
@@ -355,13 +781,13 @@ qs_status resolve_pass(int n, int RB, int WB, const PlannedPass &pp, PassDesc<R>
         return w;
     };
     std::vector<int> warps = warps_of(regs);
-    for (int r = 0; r < RB; ++r) D.lay0[r] = uint8_t(regs[r]);
-    for (int w = 0; w < WB; ++w) D.lay0[RB + w] = uint8_t(warps[w]);
+    D.lay0 = pack_layout(regs, warps);
 
-    int nops = 0;
+    ops_out.clear();
+    int n_hb = 0;
     auto push = [&](const FOp<R> &f) -> bool {
-        if (nops >= MAX_OPS) return false;
-        D.ops[nops++] = f;
+        if (int(ops_out.size()) >= MAX_OPS) return false;
+        ops_out.push_back(f);
         return true;
     };
     for (size_t k = 0; k < m; ++k) {
@@ -385,8 +811,8 @@ qs_status resolve_pass(int n, int RB, int WB, const PlannedPass &pp, PassDesc<R>
             warps = warps_of(regs);
             FOp<R> x{};
             x.type = OP_XPOSE;
-            for (int r = 0; r < RB; ++r) x.lay[r] = uint8_t(regs[r]);
-            for (int w = 0; w < WB; ++w) x.lay[RB + w] = uint8_t(warps[w]);
+            x.lay = pack_layout(regs, warps);
+            D.has_xpose = 1;
             if (!push(x)) return QS_EUNSUPPORTED;
         }
         FOp<R> f{};
@@ -395,8 +821,8 @@ qs_status resolve_pass(int n, int RB, int WB, const PlannedPass &pp, PassDesc<R>
             if (!((o.cmask >> b) & 1)) continue;
             const int val = int((o.cval >> b) & 1);
             if (b < LB) {
-                f.tmask |= uint8_t(1u << b);
-                if (val) f.tval |= uint8_t(1u << b);
+                f.tmask |= uint16_t(1u << b);
+                if (val) f.tval |= uint16_t(1u << b);
             } else if (hidx.count(b)) {
                 const int i = hidx[b];
                 auto it = std::find(regs.begin(), regs.end(), i);
@@ -406,8 +832,8 @@ qs_status resolve_pass(int n, int RB, int WB, const PlannedPass &pp, PassDesc<R>
                     if (val) f.rval |= uint8_t(1u << r);
                 } else {
                     const int w = int(std::find(warps.begin(), warps.end(), i) - warps.begin());
-                    f.tmask |= uint8_t(1u << (LB + w));
-                    if (val) f.tval |= uint8_t(1u << (LB + w));
+                    f.tmask |= uint16_t(1u << (LB + w));
+                    if (val) f.tval |= uint16_t(1u << (LB + w));
                 }
             } else {
                 f.omask |= uint64_t(1) << b;
@@ -422,6 +848,8 @@ qs_status resolve_pass(int n, int RB, int WB, const PlannedPass &pp, PassDesc<R>
                 if (o.phase_on) { d0r = 1; d0i = 0; } else { d1r = 1; d1i = 0; }
             }
             f.u[0] = R(d0r); f.u[1] = R(d0i); f.u[2] = R(d1r); f.u[3] = R(d1i);
+            // which side is the identity: 1 = d0 == 1, 2 = d1 == 1, 0 = neither
+            f.cls = uint8_t(o.cls == GC_PHASE ? (o.phase_on ? 1 : 2) : 0);
             const int b = o.bit;
             if (b < LB) { f.tsel = 1; f.tpos = uint8_t(b); }
             else if (hidx.count(b)) {
@@ -434,7 +862,11 @@ qs_status resolve_pass(int n, int RB, int WB, const PlannedPass &pp, PassDesc<R>
                 }
             } else { f.tsel = 2; f.tpos = uint8_t(b); }
         } else {
-            f.cls = uint8_t(o.cls);
+            f.cls = uint8_t(o.cls == GC_X ? GC_X : GC_GEN);
+            if (o.kind == QS_GATE_H && o.cmask == 0) {
+                f.cls = uint8_t(GC_HB);
+                ++n_hb;
+            }
             for (int k2 = 0; k2 < 8; ++k2) f.u[k2] = R(o.u[k2]);
             if (o.bit < LB) { f.type = OP_LANE; f.tpos = uint8_t(o.bit); }
             else {
@@ -444,7 +876,11 @@ qs_status resolve_pass(int n, int RB, int WB, const PlannedPass &pp, PassDesc<R>
         }
         if (!push(f)) return QS_EUNSUPPORTED;
     }
-    D.nops = nops;
+    D.nops = int(ops_out.size());
+    // (1/sqrt 2)^n_hb: an exact power of two when n_hb is even
+    double sc = std::ldexp(1.0, -(n_hb / 2));
+    if (n_hb & 1) sc *= 1.0 / std::sqrt(2.0);
+    D.scale = R(sc);
     return QS_OK;
 }
 
@@ -502,43 +938,84 @@ std::vector<PlannedPass> form_passes(int n, int H, int max_ops, const std::vecto
     return passes;
 }
 
-template <typename R>
-qs_status build_fused(Plan *P, int RB, const std::vector<HostOp> &ops, int max_ops,
-                      std::vector<PassDesc<R>> &out) {
+template <typename R, int RB>
+qs_status build_fused(Plan *P, const std::vector<HostOp> &ops, int max_ops,
+                      std::vector<PassDesc<R>> &out, std::vector<std::vector<FOp<R>>> &tables) {
     const int n = P->n;
-    const int WB = std::min(MAX_WB, n - LB - RB);
+    const int WB = std::min(sizeof(R) == 4 ? WB64 : MAX_WB, n - LB - RB);
     const int H = RB + WB;
     std::vector<HostOp> ex;
     expand_swaps(ops, ex);
     std::vector<PlannedPass> passes = form_passes(n, H, max_ops, ex);
     out.resize(passes.size());
+    tables.resize(passes.size());
+    size_t total = 0;
     for (size_t k = 0; k < passes.size(); ++k) {
-        qs_status st = resolve_pass<R>(n, RB, WB, passes[k], out[k]);
+        qs_status st = resolve_pass<R>(n, RB, WB, passes[k], out[k], tables[k]);
         if (st != QS_OK) return st;
+        out[k].tiles = uint64_t(1) << (n - out[k].K);
+        total += tables[k].size();
     }
+    (void)total;
     return QS_OK;
+}
+
+// Uploads the op tables of all passes on first use (planning itself needs no
+// GPU) and sizes the persistent grid.  A temporary plan (one qs_apply_circuit
+// call) takes stream-ordered memory that is released on the same stream.
+template <typename R, int RB>
+cudaError_t ensure_device(Plan *P, std::vector<PassDesc<R>> &passes,
+                          const std::vector<std::vector<FOp<R>>> &tables, cudaStream_t st) {
+    if (P->dev_ops || passes.empty()) return cudaSuccess;
+    std::vector<FOp<R>> flat;
+    std::vector<size_t> offs;
+    for (auto &t : tables) {
+        offs.push_back(flat.size());
+        flat.insert(flat.end(), t.begin(), t.end());
+    }
+    const size_t bytes = flat.size() * sizeof(FOp<R>);
+    cudaError_t e;
+    if (P->temp) {
+        e = cudaMallocAsync(&P->dev_ops, bytes, st);
+        if (e != cudaSuccess) return e;
+        P->free_stream = st;
+        e = cudaMemcpyAsync(P->dev_ops, flat.data(), bytes, cudaMemcpyHostToDevice, st);
+    } else {
+        e = cudaMalloc(&P->dev_ops, bytes);
+        if (e != cudaSuccess) return e;
+        e = cudaMemcpy(P->dev_ops, flat.data(), bytes, cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) return e;
+    for (size_t k = 0; k < passes.size(); ++k)
+        passes[k].ops = static_cast<const FOp<R> *>(P->dev_ops) + offs[k];
+    // persistent grid: resident CTAs per SM x SMs (queried once per device)
+    static int grid_cache[2][64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int &g = grid_cache[sizeof(R) == 8 ? 1 : 0][dev & 63];
+    if (g == 0) {
+        int sms = 0, per_sm = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const size_t smem_max = (size_t(1) << (LB + RB + MAX_WB)) * sizeof(cplx<R>) + MAX_OPS * sizeof(FOp<R>);
+        e = cudaFuncSetAttribute(PassKernel<R, RB>::ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_max));
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, PassKernel<R, RB>::ptr(), 32 << MAX_WB, smem_max);
+        if (e != cudaSuccess) return e;
+        g = std::max(1, sms * std::max(1, per_sm));
+    }
+    P->grid = g;
+    return cudaSuccess;
 }
 
 template <typename R, int RB>
 cudaError_t run_passes(qs_state *s, const std::vector<PassDesc<R>> &passes, Plan *P) {
-    static bool attr_done[8] = {false};
-    const int n = s->n;
     for (const PassDesc<R> &D : passes) {
-        const uint64_t tiles = uint64_t(1) << (n - D.K);
-        bool any_x = false;
-        for (int k = 0; k < D.nops; ++k) any_x |= D.ops[k].type == OP_XPOSE;
-        const size_t smem = any_x ? (size_t(1) << D.K) * sizeof(cplx<R>) : 0;
-        int dev = 0;
-        cudaGetDevice(&dev);
-        if (smem > 48 * 1024 && !attr_done[dev & 7]) {
-            cudaError_t e = cudaFuncSetAttribute(k_fused<R, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 int((size_t(1) << (LB + RB + MAX_WB)) * sizeof(cplx<R>)));
-            if (e != cudaSuccess) return e;
-            attr_done[dev & 7] = true;
-        }
+        const size_t smem = (D.has_xpose ? (size_t(1) << D.K) * sizeof(cplx<R>) : 0) +
+                            size_t(D.nops) * sizeof(FOp<R>);
+        const uint64_t grid = std::min<uint64_t>(D.tiles, uint64_t(P->grid));
         cudaError_t e = P->mark(s->stream, false);
         if (e != cudaSuccess) return e;
-        k_fused<R, RB><<<unsigned(tiles), 32u << D.WB, smem, s->stream>>>(static_cast<cplx<R> *>(s->d), D);
+        PassKernel<R, RB>::launch(unsigned(grid), 32u << D.WB, smem, s->stream, static_cast<cplx<R> *>(s->d), D);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         e = P->mark(s->stream, true);
@@ -547,13 +1024,134 @@ cudaError_t run_passes(qs_state *s, const std::vector<PassDesc<R>> &passes, Plan
     return cudaSuccess;
 }
 
-constexpr int RB64 = 5;    // complex64: 32 amplitudes per thread
-constexpr int RB128 = 4;   // complex128: 16 amplitudes per thread
+}  // namespace
+
+namespace {
+
+int lay_slot(uint32_t lay, int s) { return int((lay >> (4 * s)) & 15u); }
+
+// Complex64 kernel descriptor and op table from a planned pass: coefficient
+// vectors for FFMA2, global offsets of the first and last layouts, and the
+// read pattern of every transpose.
+void convert_c64(const PassDesc<float> &D, const std::vector<FOp<float>> &ops, PassC64 &out, std::vector<POp> &pops) {
+    constexpr int RB = RB64;
+    std::memset(&out, 0, sizeof(out));
+    out.tiles = D.tiles;
+    out.K = D.K;
+    out.WB = D.WB;
+    out.nops = D.nops;
+    out.has_xpose = D.has_xpose;
+    out.scale = D.scale;
+    std::memcpy(out.tile_pos, D.tile_pos, sizeof(out.tile_pos));
+    const int WB = D.WB;
+    auto offsets = [&](uint32_t lay, uint64_t *reg, uint64_t *warp) {
+        for (int j = 0; j < 32; ++j) {
+            uint64_t o = 0;
+            for (int r = 0; r < RB; ++r)
+                if ((j >> r) & 1) o |= uint64_t(1) << D.hpos[lay_slot(lay, r)];
+            reg[j] = o;
+        }
+        for (int w = 0; w < 4; ++w) warp[w] = w < WB ? uint64_t(1) << D.hpos[lay_slot(lay, RB + w)] : 0;
+    };
+    uint32_t lay = D.lay0;
+    offsets(lay, out.ld_reg, out.ld_warp);
+    pops.assign(ops.size(), POp{});
+    for (size_t k = 0; k < ops.size(); ++k) {
+        const FOp<float> &f = ops[k];
+        POp &q = pops[k];
+        q.type = f.type; q.cls = f.cls; q.tsel = f.tsel; q.tpos = f.tpos;
+        q.rmask = f.rmask; q.rval = f.rval; q.tmask = f.tmask; q.tval = f.tval;
+        q.omask = f.omask; q.oval = f.oval;
+        if (f.type == OP_XPOSE) {
+            // position of each high tile bit in the old tile order
+            // (register index bits above the warp bits, warp bits above the lanes)
+            int oldpos[16];
+            for (int r = 0; r < RB; ++r) oldpos[lay_slot(lay, r)] = LB + WB + r;
+            for (int w = 0; w < WB; ++w) oldpos[lay_slot(lay, RB + w)] = LB + w;
+            const uint32_t nl = f.lay;
+            uint16_t rd[32];
+            for (int j = 0; j < 32; ++j) {
+                uint32_t o = 0;
+                for (int r = 0; r < RB; ++r)
+                    if ((j >> r) & 1) o |= 1u << oldpos[lay_slot(nl, r)];
+                rd[j] = uint16_t(o);
+            }
+            std::memcpy(&q.c[0], rd, sizeof(rd));
+            uint8_t ow[16] = {0};
+            for (int w = 0; w < WB; ++w) ow[w] = uint8_t(oldpos[lay_slot(nl, RB + w)]);
+            std::memcpy(&q.c[8], ow, sizeof(ow));
+            lay = nl;
+        } else if (f.type == OP_DIAG) {
+            q.c[0] = make_float2(f.u[0], f.u[1]);
+            q.c[1] = make_float2(f.u[2], f.u[3]);
+        } else {
+            for (int e = 0; e < 4; ++e) q.c[e] = make_float2(f.u[2 * e], f.u[2 * e + 1]);
+        }
+    }
+    offsets(lay, out.st_reg, out.st_warp);
+}
+
+cudaError_t ensure_device_c64(Plan *P, cudaStream_t st) {
+    if (P->dev_ops || P->pc.empty()) return cudaSuccess;
+    std::vector<POp> flat;
+    std::vector<size_t> offs;
+    for (auto &t : P->pco) {
+        offs.push_back(flat.size());
+        flat.insert(flat.end(), t.begin(), t.end());
+    }
+    const size_t bytes = flat.size() * sizeof(POp);
+    cudaError_t e;
+    if (P->temp) {
+        e = cudaMallocAsync(&P->dev_ops, bytes, st);
+        if (e != cudaSuccess) return e;
+        P->free_stream = st;
+        e = cudaMemcpyAsync(P->dev_ops, flat.data(), bytes, cudaMemcpyHostToDevice, st);
+    } else {
+        e = cudaMalloc(&P->dev_ops, bytes);
+        if (e != cudaSuccess) return e;
+        e = cudaMemcpy(P->dev_ops, flat.data(), bytes, cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) return e;
+    for (size_t k = 0; k < P->pc.size(); ++k) P->pc[k].ops = static_cast<const POp *>(P->dev_ops) + offs[k];
+    static int grid_cache[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int &g = grid_cache[dev & 63];
+    if (g == 0) {
+        int sms = 0, per_sm = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const size_t smem_max = (size_t(8) << (LB + RB64 + WB64)) + MAX_OPS * sizeof(POp);
+        e = cudaFuncSetAttribute(k_fused_c64, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_max));
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_c64, 32 << WB64, smem_max);
+        if (e != cudaSuccess) return e;
+        g = std::max(1, sms * std::max(1, per_sm));
+    }
+    P->grid = g;
+    return cudaSuccess;
+}
+
+cudaError_t run_passes_c64(qs_state *s, Plan *P) {
+    for (const PassC64 &D : P->pc) {
+        const size_t smem = (D.has_xpose ? (size_t(8) << D.K) : 0) + size_t(D.nops) * sizeof(POp);
+        const uint64_t grid = std::min<uint64_t>(D.tiles, uint64_t(P->grid));
+        cudaError_t e = P->mark(s->stream, false);
+        if (e != cudaSuccess) return e;
+        k_fused_c64<<<unsigned(grid), 32u << D.WB, smem, s->stream>>>(static_cast<float2 *>(s->d), D);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        e = P->mark(s->stream, true);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
 
 }  // namespace
 
-qs_status plan_build(int n, qs_dtype dt, const std::vector<HostOp> &ops, const qs_exec_opts &o, Plan **out) {
+qs_status plan_build(int n, qs_dtype dt, const std::vector<HostOp> &ops, const qs_exec_opts &o, Plan **out,
+                     bool temp) {
     Plan *P = new Plan();
+    P->temp = temp;
     P->n = n;
     P->dt = dt;
     P->n_gates = int64_t(ops.size());
@@ -563,9 +1161,18 @@ qs_status plan_build(int n, qs_dtype dt, const std::vector<HostOp> &ops, const q
     if (!P->fused) {
         P->ops = ops;
     } else {
-        qs_status st = dt == QS_C64 ? build_fused<float>(P, RB64, ops, max_ops, P->pf)
-                                    : build_fused<double>(P, RB128, ops, max_ops, P->pd);
-        if (st != QS_OK) { delete P; return fail(st, "fusion planner: pass too large"); }
+        qs_status st = dt == QS_C64 ? build_fused<float, RB64>(P, ops, max_ops, P->pf, P->of)
+                                    : build_fused<double, RB128>(P, ops, max_ops, P->pd, P->od);
+        if (st == QS_OK && dt == QS_C64) {
+            P->pc.resize(P->pf.size());
+            P->pco.resize(P->pf.size());
+            for (size_t k = 0; k < P->pf.size(); ++k) convert_c64(P->pf[k], P->of[k], P->pc[k], P->pco[k]);
+        }
+        if (st != QS_OK) {
+            delete P;
+            if (st == QS_EUNSUPPORTED) return fail(st, "fusion planner: pass too large");
+            return st;
+        }
     }
     *out = P;
     return QS_OK;
@@ -582,9 +1189,11 @@ qs_status plan_run(qs_state *s, Plan *p) {
             if (e != cudaSuccess) break;
         }
     } else if (s->dt == QS_C64) {
-        e = run_passes<float, RB64>(s, p->pf, p);
+        e = ensure_device_c64(p, s->stream);
+        if (e == cudaSuccess) e = run_passes_c64(s, p);
     } else {
-        e = run_passes<double, RB128>(s, p->pd, p);
+        e = ensure_device<double, RB128>(p, p->pd, p->od, s->stream);
+        if (e == cudaSuccess) e = run_passes<double, RB128>(s, p->pd, p);
     }
     if (e != cudaSuccess) return cuda_fail(e, "circuit launch");
     return QS_OK;
@@ -624,6 +1233,46 @@ qs_status plan_timing(Plan *p, double *ms, int64_t *launches) {
     if (launches) *launches = int64_t(p->ev_used / 2);
     p->ev_used = 0;
     return QS_OK;
+}
+
+namespace {
+template <typename R>
+void describe_passes(const std::vector<PassDesc<R>> &passes, const std::vector<std::vector<FOp<R>>> &tables,
+                     std::string &out) {
+    for (size_t k = 0; k < passes.size(); ++k) {
+        const PassDesc<R> &D = passes[k];
+        int cnt[4] = {0, 0, 0, 0}, gen = 0, x = 0, hb = 0, pred = 0;
+        for (const FOp<R> &f : tables[k]) {
+            cnt[f.type]++;
+            if (f.type == OP_REG || f.type == OP_LANE) {
+                if (f.cls == GC_X) ++x;
+                else if (f.cls == GC_HB) ++hb;
+                else ++gen;
+                if (f.rmask) ++pred;
+            }
+        }
+        char line[256];
+        std::string bits;
+        for (int i = 0; i < D.K; ++i) bits += (i ? "," : "") + std::to_string(int(D.tile_pos[i]));
+        std::snprintf(line, sizeof(line),
+                      "pass %zu: K=%d WB=%d reg=%d lane=%d diag=%d xpose=%d (gen=%d x=%d hb=%d reg-controlled=%d) bits=[%s]\n",
+                      k, D.K, D.WB, cnt[OP_REG], cnt[OP_LANE], cnt[OP_DIAG], cnt[OP_XPOSE], gen, x, hb, pred,
+                      bits.c_str());
+        out += line;
+    }
+}
+}  // namespace
+
+std::string plan_describe(const Plan *p) {
+    std::string out;
+    char head[160];
+    std::snprintf(head, sizeof(head), "plan: n=%d dtype=%s gates=%lld fused=%d\n", p->n,
+                  p->dt == QS_C64 ? "c64" : "c128", (long long)p->n_gates, int(p->fused));
+    out += head;
+    if (!p->fused) return out;
+    if (p->dt == QS_C64) describe_passes<float>(p->pf, p->of, out);
+    else describe_passes<double>(p->pd, p->od, out);
+    return out;
 }
 
 int plan_n(const Plan *p) { return p->n; }

@@ -117,13 +117,15 @@ cudaError_t launch_scale(qs_state *s, const double *dev_norm);
 
 // Fused circuits (qs_fused.cu).
 struct Plan;
-qs_status plan_build(int n, qs_dtype dt, const std::vector<HostOp> &ops, const qs_exec_opts &o, Plan **out);
+qs_status plan_build(int n, qs_dtype dt, const std::vector<HostOp> &ops, const qs_exec_opts &o, Plan **out,
+                     bool temp);
 qs_status plan_run(qs_state *s, Plan *p);
 qs_status plan_set_timing(Plan *p, bool on);
 qs_status plan_timing(Plan *p, double *ms, int64_t *launches);
 void plan_destroy(Plan *p);
 void plan_counts(const Plan *p, int64_t *launches, int64_t *gates);
 int plan_n(const Plan *p);
+std::string plan_describe(const Plan *p);
 qs_dtype plan_dtype(const Plan *p);
 
 }  // namespace qs
