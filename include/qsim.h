@@ -220,6 +220,27 @@ qs_status qs_norm(qs_state *s, double *out);
 /* Divides the state by the square root of its (double precision) norm. */
 qs_status qs_renormalize(qs_state *s);
 
+/* Norm of a state without any allocation, for callers that cannot allocate
+ * device memory at the point they need it (a framework that owns the whole
+ * device memory budget through its own pool, a latency-critical loop in which
+ * cudaMalloc/cudaFree would synchronize the device, a component that may not
+ * call the allocator at all).  The paper has no counterpart: this is a
+ * service of the library, not a step of the method.
+ *
+ * dev_state: 2^n amplitudes of dtype dt in device memory (16-byte aligned);
+ * dev_out: one double in device memory that receives sum_i |alpha_i|^2.
+ * The call is enqueued on `stream` (NULL: legacy default stream) and returns
+ * without waiting.  It calls no cudaMalloc, cudaFree or other allocating
+ * routine: its partial sums (one per 2^16 amplitudes) live in a fixed
+ * 1 MiB array of this library's device memory, which every GPU that loads
+ * the library holds until the process exits.  Limit: n <= 32; larger n
+ * returns QS_ERANGE.  The first call on a device resolves the array's
+ * address (cudaGetSymbolAddress) with that device current, so make it before
+ * any stream capture.  All calls share the array: calls that overlap on the
+ * GPU (different streams, no ordering between them) race and may return
+ * wrong sums; order them on one stream or with events. */
+qs_status qs_norm_noalloc(const void *dev_state, int n, qs_dtype dt, double *dev_out, void *stream);
+
 /* --------------------------------------------------------------------- */
 /* Host copies (checkpoint / restore)                                      */
 /* --------------------------------------------------------------------- */

@@ -87,6 +87,7 @@ _SIGS = {
     "qs_inner": [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(C128)],
     "qs_norm": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)],
     "qs_renormalize": [ctypes.c_void_p],
+    "qs_norm_noalloc": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p],
     "qs_copy_out": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t],
     "qs_copy_in": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t],
 }
