@@ -265,24 +265,39 @@ def main():
     ms_per_step = total_ms / args.steps
     value = world * upd / (ms_per_step / 1e3)
 
-    # roofline of the dominant kernel (the fused pass, or the pair sweep)
+    # roofline of the dominant kernel (the fused pass, or the pair sweep),
+    # measured on its own launches with per-launch CUDA events
     peak_gbs, peak_src = measured_peaks()
+    sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
     per_launch_ms = kern_ms / max(1, kern_n)
-    bytes_per_launch = 2 * (amp_bytes << n)   # one read and one write of the state
-    achieved = bytes_per_launch / (per_launch_ms / 1e3) / 1e9
+    launches_per_step = kern_n / args.steps
     if args.no_fuse:
-        # unfused: algorithmic bytes = 2 x touched amplitudes per gate
-        tb = sum(2 * amp_bytes * (1 << (n - len(g.controls))) for g in gates)
-        achieved = tb * args.steps / (kern_ms / 1e3) / 1e9
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
-            "frac": achieved / peak_gbs if peak_gbs else None, "traffic": None,
-            "kernel": "k_fused" if not args.no_fuse else "k_pair",
-            "peak_source": peak_src, "launches_timed": kern_n, "kernel_ms_per_step": kern_ms / args.steps}
-    # FP32/FP64 multiply-add work of the circuit, for the ALU view of the same kernel
-    fma_per_amp = 8
-    n1q = sum(1 for g in gates if g.kind == "MATRIX")
-    flops = 2 * fma_per_amp * n1q * (1 << n)
-    roof["alu_tflops"] = flops * args.steps / (kern_ms / 1e3) / 1e12
+        # algorithmic bytes: one read and one write of every touched amplitude
+        bytes_step = sum(2 * amp_bytes * (1 << (n - len(g.controls))) for g in gates)
+    else:
+        bytes_step = launches_per_step * 2 * (amp_bytes << n)   # one read + one write per pass
+    flops_step = sum(16 * (1 << n) for g in gates if g.kind == "MATRIX")   # 8 multiply-adds per amplitude
+    kern_s_step = kern_ms / args.steps / 1e3
+    hbm_view = {"achieved": bytes_step / kern_s_step / 1e9, "peak": peak_gbs, "unit": "GB/s",
+                "frac": bytes_step / kern_s_step / 1e9 / peak_gbs, "peak_source": peak_src}
+    if args.dtype == "c64":
+        alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12     # FP32 lanes x 2 flops x SM clock
+        alu_src = "152 SMs x 128 FP32 lanes x 2 flops x %.0f MHz (measured SM clock)" % sm_mhz
+    else:
+        alu_peak = 1.25                                   # nominal FP64 rate of the part
+        alu_src = "nominal FP64 1.25 TFLOP/s"
+    alu_view = {"achieved": flops_step / kern_s_step / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": flops_step / kern_s_step / 1e12 / alu_peak, "peak_source": alu_src}
+    t_hbm = bytes_step / (peak_gbs * 1e9)
+    t_alu = flops_step / (alu_peak * 1e12)
+    main = alu_view if t_alu > t_hbm else hbm_view
+    roof = {"bound": "alu" if t_alu > t_hbm else "hbm", "achieved": main["achieved"], "peak": main["peak"],
+            "unit": main["unit"], "frac": main["frac"], "traffic": None,
+            "kernel": ("k_fused_c64" if args.dtype == "c64" else "k_fused<double,4>") if not args.no_fuse else "k_pair",
+            "peak_source": main["peak_source"], "launches_timed": kern_n,
+            "kernel_ms_per_launch": per_launch_ms, "kernel_ms_per_step": kern_ms / args.steps,
+            "hbm_view": hbm_view, "alu_view": alu_view}
+    bytes_per_launch = 2 * (amp_bytes << n)
 
     line = {
         "metric": "amp-updates/s", "value": value, "unit": "amp-updates/s",
@@ -291,8 +306,7 @@ def main():
         "vs_baseline": None, "dtype": "f32" if args.dtype == "c64" else "f64",
         "data": "synthetic", "config": workload_config(args, world),
         "gates_per_s": world * len(gates) / (ms_per_step / 1e3),
-        "hbm_gbs_algorithmic": world * plan.launches * bytes_per_launch / (ms_per_step / 1e3) / 1e9
-        if not args.no_fuse else None,
+        "hbm_gbs_algorithmic": world * bytes_step / (ms_per_step / 1e3) / 1e9,
         "passes_per_step": plan.launches,
         "roofline": roof,
         "gpu_launches": args.steps * (plan.launches + 1),

@@ -242,6 +242,71 @@ qs_status qs_renormalize(qs_state *s);
 qs_status qs_norm_noalloc(const void *dev_state, int n, qs_dtype dt, double *dev_out, void *stream);
 
 /* --------------------------------------------------------------------- */
+/* Noisy trajectories, Sec. 3 (error model) and Sec. 4.3.1 / 5.2 / 5.3     */
+/* (pure-state Monte Carlo: each run draws its own errors; the paper       */
+/* averages 1000-10000 runs)                                                */
+/* --------------------------------------------------------------------- */
+
+/* Error model of a batch.
+ *   p      probability of a flip per qubit per noisy step (Sec. 3.1)
+ *   sigma  standard deviation (rad) of the Gaussian deviation added to every
+ *          gate angle (Sec. 3.2); gates without angles (MATRIX, SWAP, H, X,
+ *          Y, Z) are not deviated: write H as URP1(pi/4, pi) and NOT as
+ *          URP1(pi/2, pi) to deviate them as the paper does
+ *   mode   QS_NOISE_FLIPS: a flip is X or Z with equal probability;
+ *          QS_NOISE_DEPOLARIZING: X, Y or Z with equal probability (the
+ *          depolarizing channel of Sec. 3.1)
+ *   every  flips are drawn after gate step s when (s + 1) % every == 0
+ *          (1: after every gate; n: once per Hadamard layer of n gates) */
+typedef struct {
+    double p;
+    double sigma;
+    int32_t mode;
+    int32_t every;
+} qs_noise;
+
+enum { QS_NOISE_FLIPS = 0, QS_NOISE_DEPOLARIZING = 1 };
+enum { QS_TRAJ_FIDELITY = 0, QS_TRAJ_PROB = 1 };
+
+/* A group of trajectories that run the same circuit on the same width.
+ *   metric  QS_TRAJ_FIDELITY: |<U x0 | psi>|^2, the fidelity to the noiseless
+ *           output of the same circuit (Sec. 5.2); QS_TRAJ_PROB: |<target|psi>|^2
+ *           (the amplitude of the marked element, Sec. 5.3)
+ *   first   id of the group's first trajectory; trajectory first + i draws
+ *           from the Philox4x32-10 stream with counter word 0 = first + i
+ *   x0      initial basis index of each of the `count` trajectories */
+typedef struct {
+    int32_t n;
+    int32_t metric;
+    uint64_t target;
+    const qs_gate *gates;
+    size_t m;
+    uint32_t first;
+    uint32_t count;
+    const uint64_t *x0;
+} qs_traj_group;
+
+/* Runs every trajectory of every group on the current device and writes the
+ * metric of trajectory k of group g to metric[offset_g + k], offset_g being
+ * the sum of the counts of the groups before g.  Random draws (Philox4x32-10,
+ * key = seed, counter (trajectory, step, slot, stream)):
+ *   flip on qubit q after step s: block (traj, s, q, 0); flip iff word 0 <
+ *     floor(p 2^32); kind from word 1 (flips mode: X if even, Z if odd;
+ *     depolarizing: (word1 * 3) >> 32 = 0, 1, 2 for X, Y, Z);
+ *   deviation of angle a of step s: block (traj, s, 64 + a, 1); Box-Muller
+ *     g = sqrt(-2 ln u1) cos(2 pi u2) with u1 = 1 - (w0:w1 >> 11) 2^-53 and
+ *     u2 = (w2:w3 >> 11) 2^-53.
+ * stats (may be NULL) receives 4 words per trajectory: the numbers of X, Y and
+ * Z flips and the sum (mod 2^64) over flip events of the SplitMix64 finalizer
+ * of (s * 64 + q) * 4 + kind (kind 1, 2, 3 = X, Y, Z).  dt selects the state
+ * precision; draws and gate synthesis are in double precision.  Synchronous
+ * (returns when the results are on the host).  Device memory: the states of
+ * all trajectories of the largest group (count x 2^n amplitudes) plus
+ * per-step tables; QS_ENOMEM if it cannot be allocated. */
+qs_status qs_run_trajectories(const qs_traj_group *groups, int n_groups, const qs_noise *noise, uint64_t seed,
+                              qs_dtype dt, double *metric, uint64_t *stats);
+
+/* --------------------------------------------------------------------- */
 /* Host copies (checkpoint / restore)                                      */
 /* --------------------------------------------------------------------- */
 

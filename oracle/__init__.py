@@ -219,7 +219,7 @@ def gauss(seed: int, traj: int, step: int, a: int) -> float:
 def run_trajectory(n: int, gates: Sequence, p: float, sigma: float, seed: int, traj: int,
                    x0: int, mode: int = NOISE_FLIPS, every: int = 1):
     """One noisy trajectory (Sec. 3 error model); returns (state, stats) with
-    stats = [#X flips, #Y flips, #Z flips, event fold].  Decoherence acts after
+    stats = [#X flips, #Y flips, #Z flips, event fingerprint].  Decoherence acts after
     gate step s when (s + 1) % every == 0."""
     psi = np.zeros(1 << n, dtype=np.complex128)
     nz = OrNoise(p, sigma, mode, every)

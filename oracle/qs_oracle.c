@@ -412,11 +412,20 @@ double or_gauss(uint64_t seed, uint32_t traj, uint32_t step, uint32_t a)
     return sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
 }
 
+/* SplitMix64 finalizer (S. Vigna, "SplitMix64", public domain): a bijective
+ * 64-bit mixing function, used to fingerprint flip events. */
+static uint64_t mix64(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
 /* Runs trajectory `traj` of the noisy circuit from basis state x0; the final
  * state is left in psi.  Statistics: stats[0] = number of X flips,
- * stats[1] = Y flips, stats[2] = Z flips, stats[3] = a 64-bit fold of the
- * flip events in (step, qubit) order, h <- h * 1000003 + (s * 64 + q) * 4 + kind
- * (kind 1 = X, 2 = Y, 3 = Z). */
+ * stats[1] = Y flips, stats[2] = Z flips, stats[3] = fingerprint of the flip
+ * events: the sum (mod 2^64) of mix64((s * 64 + q) * 4 + kind) over events
+ * (kind 1 = X, 2 = Y, 3 = Z), which does not depend on their order. */
 int or_run_trajectory(double *psi_out, int n, const or_gate *g, int64_t m,
                       const or_noise *noise, uint64_t seed, uint32_t traj,
                       uint64_t x0, uint64_t *stats)
@@ -453,7 +462,7 @@ int or_run_trajectory(double *psi_out, int n, const or_gate *g, int64_t m,
             e.target = q; e.target2 = -1; e.param = -1;
             apply_gate_angles(psi, n, &e, e.angle);
             stats[kind - 1] += 1;
-            stats[3] = stats[3] * 1000003ull + ((uint64_t)s * 64u + (uint64_t)q) * 4u + (uint64_t)kind;
+            stats[3] += mix64(((uint64_t)s * 64u + (uint64_t)q) * 4u + (uint64_t)kind);
         }
     }
     return 0;

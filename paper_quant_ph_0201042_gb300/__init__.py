@@ -52,6 +52,22 @@ class QsExecOpts(ctypes.Structure):
                 ("reserved", ctypes.c_int32 * 6)]
 
 
+class QsNoise(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_double), ("sigma", ctypes.c_double), ("mode", ctypes.c_int32),
+                ("every", ctypes.c_int32)]
+
+
+class QsTrajGroup(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("metric", ctypes.c_int32), ("target", ctypes.c_uint64),
+                ("gates", ctypes.POINTER(QsGate)), ("m", ctypes.c_size_t), ("first", ctypes.c_uint32),
+                ("count", ctypes.c_uint32), ("x0", ctypes.POINTER(ctypes.c_uint64))]
+
+
+NOISE_FLIPS = 0
+NOISE_DEPOLARIZING = 1
+TRAJ_FIDELITY = 0
+TRAJ_PROB = 1
+
 assert ctypes.sizeof(QsGate) == 112
 
 _lib: Optional[ctypes.CDLL] = None
@@ -88,6 +104,8 @@ _SIGS = {
     "qs_norm": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)],
     "qs_renormalize": [ctypes.c_void_p],
     "qs_norm_noalloc": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p],
+    "qs_run_trajectories": [ctypes.POINTER(QsTrajGroup), ctypes.c_int, ctypes.POINTER(QsNoise), ctypes.c_uint64,
+                            ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)],
     "qs_copy_out": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t],
     "qs_copy_in": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t],
 }
@@ -323,3 +341,50 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def run_trajectories(groups: Sequence, p: float, sigma: float, seed: int, dtype: str = "c64",
+                     mode: int = NOISE_FLIPS, every: int = 1, with_stats: bool = True):
+    """Runs batches of noisy trajectories (qs_run_trajectories).
+
+    groups: sequence of dicts with keys n, gates, x0 (array of basis indices),
+    first (trajectory id of the first), metric ('fidelity' or 'prob') and
+    target (for 'prob').  Returns (metric array, stats array of shape (T, 4)
+    or None) in group order."""
+    keep = []
+    arr = (QsTrajGroup * max(1, len(groups)))()
+    total = 0
+    for k, g in enumerate(groups):
+        ga = gates_to_abi(g["gates"])
+        x0 = np.ascontiguousarray(g["x0"], dtype=np.uint64)
+        keep += [ga, x0]
+        c = arr[k]
+        c.n = g["n"]
+        c.metric = TRAJ_FIDELITY if g.get("metric", "fidelity") == "fidelity" else TRAJ_PROB
+        c.target = int(g.get("target", 0))
+        c.gates = ga
+        c.m = len(g["gates"])
+        c.first = int(g["first"])
+        c.count = int(x0.size)
+        c.x0 = x0.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+        total += x0.size
+    nz = QsNoise(p, sigma, mode, every)
+    met = np.zeros(max(1, total), dtype=np.float64)
+    st = np.zeros((max(1, total), 4), dtype=np.uint64) if with_stats else None
+    check(lib().qs_run_trajectories(arr, len(groups), ctypes.byref(nz), seed, DTYPES[dtype],
+                                    met.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                    st.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)) if st is not None else None))
+    return met[:total], (st[:total] if st is not None else None)
+
+
+def batch_groups(batch) -> list:
+    """Groups of a workloads.TrajectoryBatch in the form run_trajectories takes."""
+    out = []
+    for k in range(len(batch.widths)):
+        f, c = batch.first[k], batch.count[k]
+        g = {"n": batch.widths[k], "gates": batch.circuits[k], "x0": batch.x0[f:f + c], "first": f}
+        if batch.kinds[k] == "grover":
+            g["metric"] = "prob"
+            g["target"] = batch.marked[k]
+        out.append(g)
+    return out
