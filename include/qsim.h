@@ -307,6 +307,39 @@ qs_status qs_run_trajectories(const qs_traj_group *groups, int n_groups, const q
                               qs_dtype dt, double *metric, uint64_t *stats);
 
 /* --------------------------------------------------------------------- */
+/* Gradients by the adjoint (reverse) sweep                                */
+/* --------------------------------------------------------------------- */
+
+enum { QS_OBS_PAULI = 0, QS_OBS_FIDELITY = 1 };
+
+/* Cost whose gradient is taken.
+ *   QS_OBS_PAULI     E = <psi| P |psi> for the Pauli string `pauli` (n
+ *                    characters from I, X, Y, Z, character q on qubit q)
+ *   QS_OBS_FIDELITY  E = |<phi|psi>|^2 with phi the state `ref` (same n and
+ *                    dtype as the workspace, on the same stream) */
+typedef struct {
+    int32_t kind;
+    int32_t pad;
+    const char *pauli;
+    const qs_state *ref;
+} qs_observable;
+
+/* Runs the circuit g[0..m-1] from |0...0> on the workspace s, with every gate
+ * whose `param` is >= 0 taking theta[0] = params[param] (and, for URP1,
+ * theta[1] = params[param + 1]); writes E to *value and dE/dparams to
+ * grad[0..n_params-1] (parameters no gate uses get 0).  The gradient comes
+ * from one reverse sweep: with lambda = O psi (or phi <phi|psi>), each
+ * parameterised gate U_j contributes 2 Re <lambda_j| (dU_j U_j^dagger) |psi_j>,
+ * then psi and lambda are uncomputed with U_j^dagger, so no intermediate
+ * state is stored.  A deviated angle theta + x has the same derivative with
+ * respect to x as with respect to theta.  Differentiable kinds: RY, RZ, UR,
+ * UP1, UP2, URP1 (QS_EUNSUPPORTED for a parameter on another kind).  On
+ * return the workspace holds the uncomputed state (close to |0...0>).  Uses
+ * one extra state-sized buffer and per-gate partial sums.  Synchronous. */
+qs_status qs_adjoint_grad(qs_state *s, const qs_gate *g, size_t m, const double *params, size_t n_params,
+                          const qs_observable *obs, double *value, double *grad);
+
+/* --------------------------------------------------------------------- */
 /* Host copies (checkpoint / restore)                                      */
 /* --------------------------------------------------------------------- */
 

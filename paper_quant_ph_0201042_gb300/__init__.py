@@ -63,6 +63,13 @@ class QsTrajGroup(ctypes.Structure):
                 ("count", ctypes.c_uint32), ("x0", ctypes.POINTER(ctypes.c_uint64))]
 
 
+class QsObservable(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("pad", ctypes.c_int32), ("pauli", ctypes.c_char_p),
+                ("ref", ctypes.c_void_p)]
+
+
+OBS_PAULI = 0
+OBS_FIDELITY = 1
 NOISE_FLIPS = 0
 NOISE_DEPOLARIZING = 1
 TRAJ_FIDELITY = 0
@@ -106,6 +113,9 @@ _SIGS = {
     "qs_norm_noalloc": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p],
     "qs_run_trajectories": [ctypes.POINTER(QsTrajGroup), ctypes.c_int, ctypes.POINTER(QsNoise), ctypes.c_uint64,
                             ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)],
+    "qs_adjoint_grad": [ctypes.c_void_p, ctypes.POINTER(QsGate), ctypes.c_size_t, ctypes.POINTER(ctypes.c_double),
+                        ctypes.c_size_t, ctypes.POINTER(QsObservable), ctypes.POINTER(ctypes.c_double),
+                        ctypes.POINTER(ctypes.c_double)],
     "qs_copy_out": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t],
     "qs_copy_in": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t],
 }
@@ -388,3 +398,57 @@ def batch_groups(batch) -> list:
             g["target"] = batch.marked[k]
         out.append(g)
     return out
+
+
+def adjoint_grad(work: "State", gates: Sequence, params, pauli: Optional[str] = None,
+                 ref: Optional["State"] = None):
+    """(E, dE/dparams) by the adjoint reverse sweep (qs_adjoint_grad).  E is
+    <psi|pauli|psi> or, with ref, |<ref|psi>|^2; psi is the circuit applied to
+    |0...0> in `work` with gate angles taken from params by each gate's param
+    index."""
+    arr = gates_to_abi(gates)
+    prm = np.ascontiguousarray(np.asarray(params, dtype=np.float64).reshape(-1))
+    grad = np.zeros(max(1, prm.size))
+    val = ctypes.c_double()
+    obs = QsObservable()
+    if ref is not None:
+        obs.kind = OBS_FIDELITY
+        obs.ref = ref.handle
+    else:
+        obs.kind = OBS_PAULI
+        obs.pauli = pauli.encode()
+    check(lib().qs_adjoint_grad(work.handle, arr, len(gates), prm.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                prm.size, ctypes.byref(obs), ctypes.byref(val),
+                                grad.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return val.value, grad[:prm.size]
+
+
+def _make_adjoint_function():
+    import torch
+
+    class AdjointExpectation(torch.autograd.Function):
+        """E(params) for a parameterised circuit, differentiated by the
+        library's adjoint reverse sweep.  forward(params, work, gates, pauli,
+        ref) returns E as a 0-d float64 tensor; backward returns
+        grad_output * dE/dparams for params (None for the others)."""
+
+        @staticmethod
+        def forward(ctx, params, work, gates, pauli=None, ref=None):
+            val, grad = adjoint_grad(work, gates, params.detach().cpu().numpy(), pauli=pauli, ref=ref)
+            ctx.save_for_backward(torch.from_numpy(grad).to(params.device, params.dtype))
+            return torch.tensor(val, dtype=torch.float64, device=params.device)
+
+        @staticmethod
+        def backward(ctx, grad_output):
+            (g,) = ctx.saved_tensors
+            return grad_output.to(g.dtype) * g, None, None, None, None
+
+    return AdjointExpectation
+
+
+def __getattr__(name):
+    if name == "AdjointExpectation":
+        fn = _make_adjoint_function()
+        globals()["AdjointExpectation"] = fn
+        return fn
+    raise AttributeError(name)

@@ -1,0 +1,400 @@
+// Gradients of an expectation value with respect to gate angles by one
+// reverse sweep over the circuit (the differentiation pattern built on the
+// paper's evolution steps, Sec. 2.2).
+//
+// With psi_j = U_j ... U_1 |0>, E = <psi_N|O|psi_N> and lambda_j =
+// (U_N ... U_{j+1})^dagger O psi_N, the derivative with respect to an angle
+// of U_j is 2 Re <lambda_j| dU_j U_j^dagger |psi_j>: the 2x2 generator
+// G = dU U^dagger acts on the target pair (on the pairs whose controls hold,
+// for a controlled gate).  Walking j = N..1, each step computes that sum from
+// the pairs of psi_j and lambda_j and, in the same pass, uncomputes both
+// vectors with U_j^dagger, so no intermediate state is ever stored.  Every
+// pair is handled by one thread that reads the four amplitudes before writing
+// any (the in-place rule of Sec. 2.2.1).
+//
+// Sums: each block adds its pairs (complex64: single-precision per thread,
+// then double across threads; complex128: double throughout) and writes one
+// partial per angle; fixed-order reductions then give one sum per angle and
+// one per parameter.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "qs_internal.cuh"
+
+namespace qs {
+
+namespace {
+
+constexpr int THREADS = 256;
+enum AdjClass : int32_t { AC_GEN = 0, AC_REAL = 1, AC_DIAG = 2, AC_X = 3, AC_SWAP = 4 };
+
+struct AdjStep {
+    int32_t cls;
+    int32_t nang;          // angles whose derivative is accumulated (0, 1, 2)
+    int32_t slot0, slot1;  // partial-sum slots of the angles
+    uint64_t tbit, tbit2;  // target (and second SWAP) index bits as masks
+    uint64_t cval;
+    double ui[8];          // U^dagger
+    double g0[8], g1[8];   // generators dU U^dagger of the angles
+    uint8_t pos[64];       // fixed bit positions, ascending
+    int32_t nfixed;
+    int32_t pad;
+};
+
+__device__ __forceinline__ uint64_t deposit(uint64_t p, const uint8_t *pos, int nf) {
+    for (int k = 0; k < nf; ++k) {
+        const uint64_t low = (uint64_t(1) << pos[k]) - 1;
+        p = ((p & ~low) << 1) | (p & low);
+    }
+    return p;
+}
+
+template <typename R>
+__device__ __forceinline__ R rdot(cplx<R> a, cplx<R> b) { return a.x * b.x + a.y * b.y; }   // Re(conj(a) b)
+
+template <typename R>
+__device__ __forceinline__ cplx<R> cmat(const double *u, int k) { return mk<R>(R(u[2 * k]), R(u[2 * k + 1])); }
+
+__device__ __forceinline__ double blk_sum(double v) {
+    __shared__ double sh[THREADS / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    v = 0.0;
+    if (w == 0) {
+        v = l < THREADS / 32 ? sh[l] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    }
+    return v;
+}
+
+// One reverse step: gradient partial sums of the step's angles from
+// (psi_j, lambda_j), then psi <- U^dagger psi, lambda <- U^dagger lambda.
+template <typename R>
+__global__ void __launch_bounds__(THREADS) k_adj(cplx<R> *__restrict__ psi, cplx<R> *__restrict__ lam, int n,
+                                                 const AdjStep *__restrict__ dp, double *__restrict__ part) {
+    const AdjStep &d = *dp;
+    const int nf = d.nfixed;
+    const uint64_t count = uint64_t(1) << (n - nf);
+    const cplx<R> u00 = cmat<R>(d.ui, 0), u01 = cmat<R>(d.ui, 1), u10 = cmat<R>(d.ui, 2), u11 = cmat<R>(d.ui, 3);
+    const cplx<R> a00 = cmat<R>(d.g0, 0), a01 = cmat<R>(d.g0, 1), a10 = cmat<R>(d.g0, 2), a11 = cmat<R>(d.g0, 3);
+    const cplx<R> b00 = cmat<R>(d.g1, 0), b01 = cmat<R>(d.g1, 1), b10 = cmat<R>(d.g1, 2), b11 = cmat<R>(d.g1, 3);
+    R acc0 = 0, acc1 = 0;
+    for (uint64_t p = uint64_t(blockIdx.x) * THREADS + threadIdx.x; p < count; p += uint64_t(gridDim.x) * THREADS) {
+        const uint64_t i0 = deposit(p, d.pos, nf) | d.cval;
+        if (d.cls == AC_SWAP) {
+            const uint64_t ia = i0 | d.tbit, ib = i0 | d.tbit2;
+            cplx<R> t = psi[ia]; psi[ia] = psi[ib]; psi[ib] = t;
+            t = lam[ia]; lam[ia] = lam[ib]; lam[ib] = t;
+            continue;
+        }
+        const uint64_t i1 = i0 | d.tbit;
+        const cplx<R> px = psi[i0], py = psi[i1], lx = lam[i0], ly = lam[i1];
+        if (d.nang > 0) {
+            acc0 += rdot<R>(lx, cmad2<R>(a00, px, a01, py)) + rdot<R>(ly, cmad2<R>(a10, px, a11, py));
+            if (d.nang > 1)
+                acc1 += rdot<R>(lx, cmad2<R>(b00, px, b01, py)) + rdot<R>(ly, cmad2<R>(b10, px, b11, py));
+        }
+        if (d.cls == AC_X) {
+            psi[i0] = py; psi[i1] = px; lam[i0] = ly; lam[i1] = lx;
+        } else if (d.cls == AC_DIAG) {
+            psi[i0] = cmul<R>(u00, px); psi[i1] = cmul<R>(u11, py);
+            lam[i0] = cmul<R>(u00, lx); lam[i1] = cmul<R>(u11, ly);
+        } else if (d.cls == AC_REAL) {
+            psi[i0] = rmad2<R>(u00.x, px, u01.x, py); psi[i1] = rmad2<R>(u10.x, px, u11.x, py);
+            lam[i0] = rmad2<R>(u00.x, lx, u01.x, ly); lam[i1] = rmad2<R>(u10.x, lx, u11.x, ly);
+        } else {
+            psi[i0] = cmad2<R>(u00, px, u01, py); psi[i1] = cmad2<R>(u10, px, u11, py);
+            lam[i0] = cmad2<R>(u00, lx, u01, ly); lam[i1] = cmad2<R>(u10, lx, u11, ly);
+        }
+    }
+    if (d.nang > 0) {
+        const double s0 = blk_sum(double(acc0));
+        if (threadIdx.x == 0) part[uint64_t(d.slot0) * gridDim.x + blockIdx.x] = s0;
+        if (d.nang > 1) {
+            const double s1 = blk_sum(double(acc1));
+            if (threadIdx.x == 0) part[uint64_t(d.slot1) * gridDim.x + blockIdx.x] = s1;
+        }
+    }
+}
+
+// lambda = P psi for a Pauli string: (P psi)[i ^ flip] = i^ny (-1)^popcount(i & sign) psi[i]
+template <typename R>
+__global__ void __launch_bounds__(THREADS) k_pauli_apply(const cplx<R> *__restrict__ psi, cplx<R> *__restrict__ lam,
+                                                         uint64_t N, uint64_t flip, uint64_t sign, int ny) {
+    for (uint64_t i = uint64_t(blockIdx.x) * THREADS + threadIdx.x; i < N; i += uint64_t(gridDim.x) * THREADS) {
+        cplx<R> v = psi[i];
+        if (__popcll(i & sign) & 1) v = mk<R>(-v.x, -v.y);
+        switch (ny & 3) {
+        case 1: v = mk<R>(-v.y, v.x); break;
+        case 2: v = mk<R>(-v.x, -v.y); break;
+        case 3: v = mk<R>(v.y, -v.x); break;
+        default: break;
+        }
+        lam[i ^ flip] = v;
+    }
+}
+
+// lambda = c phi
+template <typename R>
+__global__ void __launch_bounds__(THREADS) k_scale_copy(const cplx<R> *__restrict__ phi, cplx<R> *__restrict__ lam,
+                                                        uint64_t N, double cr, double ci) {
+    const cplx<R> c = mk<R>(R(cr), R(ci));
+    for (uint64_t i = uint64_t(blockIdx.x) * THREADS + threadIdx.x; i < N; i += uint64_t(gridDim.x) * THREADS)
+        lam[i] = cmul<R>(c, phi[i]);
+}
+
+// Sum of each slot's block partials, in order.
+__global__ void __launch_bounds__(THREADS) k_slot_sums(const double *__restrict__ part, int nblk, double *__restrict__ out) {
+    double v = 0.0;
+    for (int k = threadIdx.x; k < nblk; k += THREADS) v += part[uint64_t(blockIdx.x) * nblk + k];
+    v = blk_sum(v);
+    if (threadIdx.x == 0) out[blockIdx.x] = v;
+}
+
+// grad[p] = 2 * sum of the slots of parameter p (slots sorted by parameter).
+__global__ void k_collect(const double *__restrict__ slot_sum, const int *__restrict__ first, int n_params,
+                          double *__restrict__ grad) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n_params; p += gridDim.x * blockDim.x) {
+        double v = 0.0;
+        for (int k = first[p]; k < first[p + 1]; ++k) v += slot_sum[k];
+        grad[p] = 2.0 * v;
+    }
+}
+
+// 2x2 complex products (row major, re/im pairs).
+void mul2(const double *a, const double *b, double *c) {
+    for (int r = 0; r < 2; ++r)
+        for (int q = 0; q < 2; ++q) {
+            double re = 0, im = 0;
+            for (int k = 0; k < 2; ++k) {
+                const double ar = a[2 * (2 * r + k)], ai = a[2 * (2 * r + k) + 1];
+                const double br = b[2 * (2 * k + q)], bi = b[2 * (2 * k + q) + 1];
+                re += ar * br - ai * bi;
+                im += ar * bi + ai * br;
+            }
+            c[2 * (2 * r + q)] = re;
+            c[2 * (2 * r + q) + 1] = im;
+        }
+}
+
+void dagger(const double *u, double *v) {
+    const double w[8] = {u[0], -u[1], u[4], -u[5], u[2], -u[3], u[6], -u[7]};
+    std::memcpy(v, w, sizeof(w));
+}
+
+// Generator dU/da U^dagger of angle `which` of a gate kind at angles (a, b).
+bool generator(int kind, int which, double a, double b, double *g) {
+    for (int k = 0; k < 8; ++k) g[k] = 0.0;
+    switch (kind) {
+    case QS_GATE_RY: g[2] = -0.5; g[4] = 0.5; return true;             // -(i/2) Y
+    case QS_GATE_RZ: g[1] = -0.5; g[7] = 0.5; return true;             // -(i/2) Z
+    case QS_GATE_UP1: g[7] = 1.0; return true;                         // diag(0, i)
+    case QS_GATE_UP2: g[1] = 1.0; return true;                         // diag(i, 0)
+    case QS_GATE_UR: g[2] = -1.0; g[4] = 1.0; return true;             // -i Y
+    case QS_GATE_URP1:
+        if (which == 0) { g[2] = -1.0; g[4] = 1.0; return true; }      // dU_R U_R^dagger = -i Y
+        {
+            // U_R(a) diag(0, i) U_R(a)^dagger
+            const double c = std::cos(a), s = std::sin(a);
+            const double R[8] = {c, 0, -s, 0, s, 0, c, 0};
+            const double D[8] = {0, 0, 0, 0, 0, 0, 0, 1};
+            double Rd[8], t[8];
+            dagger(R, Rd);
+            mul2(R, D, t);
+            mul2(t, Rd, g);
+            (void)b;
+            return true;
+        }
+    default:
+        return false;
+    }
+}
+
+int kind_angles(int kind) {
+    switch (kind) {
+    case QS_GATE_UP1: case QS_GATE_UP2: case QS_GATE_UR: case QS_GATE_RY: case QS_GATE_RZ: return 1;
+    case QS_GATE_URP1: return 2;
+    default: return 0;
+    }
+}
+
+struct Buf {
+    void *p = nullptr;
+    cudaStream_t s = nullptr;
+    ~Buf() { if (p) cudaFreeAsync(p, s); }
+};
+
+template <typename R>
+qs_status run_adjoint(qs_state *s, const std::vector<qs_gate> &gg, size_t n_params, const qs_observable &obs,
+                      double *value, double *grad) {
+    const int n = s->n;
+    const uint64_t N = uint64_t(1) << n;
+    cudaStream_t st = s->stream;
+    // forward
+    qs_status rc = qs_init_basis(s, 0);
+    if (rc != QS_OK) return rc;
+    rc = qs_apply_circuit(s, gg.data(), gg.size(), nullptr);
+    if (rc != QS_OK) return rc;
+    // value, and lambda = O psi
+    Buf lam;
+    lam.s = st;
+    if (cudaMallocAsync(&lam.p, sizeof(cplx<R>) * N, st) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(QS_ENOMEM, "adjoint: device allocation failed");
+    }
+    const unsigned grid = unsigned(std::min<uint64_t>((N + THREADS - 1) / THREADS, 152ull * 16));
+    if (obs.kind == QS_OBS_PAULI) {
+        rc = qs_expect(s, obs.pauli, value);
+        if (rc != QS_OK) return rc;
+        uint64_t flip = 0, sign = 0;
+        int ny = 0;
+        for (int q = 0; q < n; ++q) {
+            const uint64_t b = uint64_t(1) << (n - 1 - q);
+            if (obs.pauli[q] == 'X') flip |= b;
+            else if (obs.pauli[q] == 'Y') { flip |= b; sign |= b; ++ny; }
+            else if (obs.pauli[q] == 'Z') sign |= b;
+        }
+        k_pauli_apply<R><<<grid, THREADS, 0, st>>>(static_cast<const cplx<R> *>(s->d), static_cast<cplx<R> *>(lam.p),
+                                                   N, flip, sign, ny);
+    } else {
+        qs_c128 c;
+        rc = qs_inner(const_cast<qs_state *>(obs.ref), s, &c);
+        if (rc != QS_OK) return rc;
+        *value = c.re * c.re + c.im * c.im;
+        k_scale_copy<R><<<grid, THREADS, 0, st>>>(static_cast<const cplx<R> *>(obs.ref->d),
+                                                  static_cast<cplx<R> *>(lam.p), N, c.re, c.im);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint launch");
+    // steps, slots
+    std::vector<AdjStep> steps(gg.size());
+    std::vector<std::pair<int, int>> slot_param;   // (param, slot)
+    for (size_t j = 0; j < gg.size(); ++j) {
+        HostOp o;
+        rc = synthesize(n, gg[j], o);
+        if (rc != QS_OK) return rc;
+        AdjStep &d = steps[j];
+        std::memset(&d, 0, sizeof(d));
+        std::vector<int> pos;
+        for (int b = 0; b < 64; ++b)
+            if ((o.cmask >> b) & 1) pos.push_back(b);
+        d.cval = o.cval;
+        d.tbit = uint64_t(1) << o.bit;
+        if (o.cls == GC_SWAP) {
+            d.cls = AC_SWAP;
+            d.tbit2 = uint64_t(1) << o.bit2;
+            pos.push_back(o.bit);
+            pos.push_back(o.bit2);
+        } else {
+            pos.push_back(o.bit);
+            dagger(o.u, d.ui);
+            d.cls = o.cls == GC_X ? AC_X
+                  : (o.cls == GC_DIAG || o.cls == GC_PHASE || o.cls == GC_ID) ? AC_DIAG
+                  : o.cls == GC_REAL ? AC_REAL : AC_GEN;
+        }
+        std::sort(pos.begin(), pos.end());
+        d.nfixed = int(pos.size());
+        for (size_t k = 0; k < pos.size(); ++k) d.pos[k] = uint8_t(pos[k]);
+        if (gg[j].param >= 0) {
+            const int na = kind_angles(gg[j].kind);
+            if (na == 0) return fail(QS_EUNSUPPORTED, "adjoint: a parameter on a gate kind without angles");
+            for (int a = 0; a < na; ++a) {
+                const int pidx = gg[j].param + a;
+                if (pidx >= int(n_params)) return fail(QS_EINVAL, "adjoint: parameter index beyond n_params");
+                double *g = a == 0 ? d.g0 : d.g1;
+                generator(gg[j].kind, a, gg[j].theta[0], gg[j].theta[1], g);
+                const int slot = int(slot_param.size());
+                (a == 0 ? d.slot0 : d.slot1) = slot;
+                slot_param.push_back({pidx, slot});
+            }
+            d.nang = na;
+        }
+    }
+    const int nslot = int(slot_param.size());
+    const int nblk = RED_BLOCKS;
+    Buf part, ssum, dgrad, dfirst, dsteps;
+    for (Buf *b : {&part, &ssum, &dgrad, &dfirst, &dsteps}) b->s = st;
+    if (cudaMallocAsync(&part.p, sizeof(double) * std::max(1, nslot) * nblk, st) != cudaSuccess ||
+        cudaMallocAsync(&ssum.p, sizeof(double) * std::max(1, nslot), st) != cudaSuccess ||
+        cudaMallocAsync(&dgrad.p, sizeof(double) * std::max<size_t>(1, n_params), st) != cudaSuccess ||
+        cudaMallocAsync(&dfirst.p, sizeof(int) * (n_params + 1), st) != cudaSuccess ||
+        cudaMallocAsync(&dsteps.p, sizeof(AdjStep) * std::max<size_t>(1, steps.size()), st) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(QS_ENOMEM, "adjoint: device allocation failed");
+    }
+    // slots ordered by parameter (stable in gate order): CSR offsets
+    std::vector<std::pair<int, int>> order = slot_param;
+    std::stable_sort(order.begin(), order.end(), [](const auto &x, const auto &y) { return x.first < y.first; });
+    std::vector<int> remap(nslot), first(n_params + 1, 0);
+    for (int k = 0; k < nslot; ++k) remap[order[k].second] = k;
+    for (const auto &sp : slot_param) first[sp.first + 1]++;
+    for (size_t p = 0; p < n_params; ++p) first[p + 1] += first[p];
+    for (AdjStep &d : steps) {
+        if (d.nang > 0) d.slot0 = remap[d.slot0];
+        if (d.nang > 1) d.slot1 = remap[d.slot1];
+    }
+    e = cudaMemcpyAsync(dsteps.p, steps.data(), sizeof(AdjStep) * steps.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dfirst.p, first.data(), sizeof(int) * (n_params + 1), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint upload");
+    // reverse sweep
+    cplx<R> *psi = static_cast<cplx<R> *>(s->d);
+    cplx<R> *lp = static_cast<cplx<R> *>(lam.p);
+    for (size_t j = steps.size(); j-- > 0;) {
+        k_adj<R><<<nblk, THREADS, 0, st>>>(psi, lp, n, static_cast<const AdjStep *>(dsteps.p) + j,
+                                           static_cast<double *>(part.p));
+    }
+    if (nslot > 0) k_slot_sums<<<nslot, THREADS, 0, st>>>(static_cast<const double *>(part.p), nblk,
+                                                          static_cast<double *>(ssum.p));
+    if (n_params > 0)
+        k_collect<<<unsigned((n_params + 255) / 256), 256, 0, st>>>(static_cast<const double *>(ssum.p),
+                                                                    static_cast<const int *>(dfirst.p), int(n_params),
+                                                                    static_cast<double *>(dgrad.p));
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint launch");
+    if (n_params > 0) {
+        e = cudaMemcpyAsync(grad, dgrad.p, sizeof(double) * n_params, cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return cuda_fail(e, "adjoint results");
+    }
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint");
+    return QS_OK;
+}
+
+}  // namespace
+}  // namespace qs
+
+using namespace qs;
+
+extern "C" qs_status qs_adjoint_grad(qs_state *s, const qs_gate *g, size_t m, const double *params, size_t n_params,
+                                     const qs_observable *obs, double *value, double *grad) {
+    if (!s || !obs || !value || (m > 0 && !g) || (n_params > 0 && (!params || !grad)))
+        return fail(QS_EINVAL, "NULL argument");
+    if (n_params > (size_t(1) << 30)) return fail(QS_ERANGE, "too many parameters");
+    if (obs->kind == QS_OBS_PAULI) {
+        if (!obs->pauli || std::strlen(obs->pauli) != size_t(s->n)) return fail(QS_EINVAL, "observable: Pauli string length");
+        for (int q = 0; q < s->n; ++q)
+            if (!std::strchr("IXYZ", obs->pauli[q])) return fail(QS_EINVAL, "observable: Pauli characters");
+    } else if (obs->kind == QS_OBS_FIDELITY) {
+        if (!obs->ref || obs->ref->n != s->n || obs->ref->dt != s->dt) return fail(QS_EINVAL, "observable: reference state");
+        if (obs->ref->stream != s->stream) return fail(QS_EINVAL, "observable: reference on another stream");
+    } else {
+        return fail(QS_EINVAL, "observable: bad kind");
+    }
+    std::vector<qs_gate> gg(g, g + m);
+    for (qs_gate &x : gg) {
+        if (x.param < 0) continue;
+        const int na = kind_angles(x.kind);
+        if (x.param + std::max(na, 1) > int64_t(n_params)) return fail(QS_EINVAL, "gate parameter index beyond n_params");
+        for (int a = 0; a < na; ++a) x.theta[a] = params[x.param + a];
+    }
+    return s->dt == QS_C64 ? run_adjoint<float>(s, gg, n_params, *obs, value, grad)
+                           : run_adjoint<double>(s, gg, n_params, *obs, value, grad);
+}

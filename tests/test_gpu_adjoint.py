@@ -1,0 +1,148 @@
+"""Adjoint gradients (qs_adjoint_grad) against the oracle's parameter-shift
+rule (FP64) at n = 10, and at the full 26-qubit size against central finite
+differences of the complex128 GPU forward pass at sampled angles."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_quant_ph_0201042_gb300 as qs  # noqa: E402
+from paper_quant_ph_0201042_gb300 import build as qbuild  # noqa: E402
+
+qbuild.build()
+
+GTOL = {"c128": 1e-9, "c64": 2e-4}
+
+
+def perturbed(params, sigma, seed):
+    return params + sigma * W.rng(seed).standard_normal(params.size)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_ansatz_n10_pauli_against_parameter_shift(dtype):
+    # the gradient workload at the oracle's size: 25 layers of RY, RZ and a
+    # C-NOT ladder on 10 qubits (500 angles), observable <Z_0>
+    n = 10
+    gates, params = W.ansatz_circuit(n, 25, seed=4)
+    pauli = "Z" + "I" * (n - 1)
+    work = qs.State(n, dtype)
+    val, grad = qs.adjoint_grad(work, gates, params, pauli=pauli)
+    want_val = oracle.cost(n, gates, params, pauli=pauli)
+    want = oracle.gradient(n, gates, params, pauli=pauli, method="shift")
+    assert abs(val - want_val) < GTOL[dtype]
+    assert np.max(np.abs(grad - want)) < GTOL[dtype], np.max(np.abs(grad - want))
+    fd = oracle.gradient(n, gates, params, pauli=pauli, method="fd", h=1e-4)
+    assert np.max(np.abs(grad - fd)) < GTOL[dtype] + 1e-7
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_ansatz_n10_fidelity_to_noiseless_output(dtype):
+    # the fidelity to the noiseless output, differentiated with respect to
+    # every (deviated) angle: d/dx F(theta + x) = dF/dtheta at theta + x
+    n = 10
+    gates, params = W.ansatz_circuit(n, 25, seed=5)
+    ideal = oracle.run(n, gates)
+    x = perturbed(params, 0.05, 6)
+    ref = qs.State(n, dtype).from_numpy(ideal)
+    work = qs.State(n, dtype)
+    val, grad = qs.adjoint_grad(work, gates, x, ref=ref)
+    want_val = oracle.cost(n, gates, x, ref=ideal)
+    want = oracle.gradient(n, gates, x, ref=ideal, method="shift")
+    assert abs(val - want_val) < GTOL[dtype]
+    assert np.max(np.abs(grad - want)) < GTOL[dtype], np.max(np.abs(grad - want))
+
+
+def test_urp1_and_controlled_parameters():
+    # the paper's synthesis U_R(theta) U_P1(phi) (two angles per gate),
+    # controlled phase shifts, and a parameter shared by two gates of the same
+    # shift class (a U_R gate reusing the first U_R angle)
+    n = 6
+    r = W.rng(8)
+    gates = []
+    k = 0
+    for layer in range(3):
+        for q in range(n):
+            gates.append(W.Gate("URP1", q, angles=(0.0, 0.0), param=k))
+            k += 2
+        for q in range(n - 1):
+            gates.append(W.Gate("UP1", q + 1, controls={q: 1}, angles=(0.0,), param=k))
+            k += 1
+    gates.append(W.Gate("UR", 3, angles=(0.0,), param=0))
+    params = r.uniform(-math.pi, math.pi, size=k)
+    pauli = "XZYIZX"
+    want = oracle.gradient(n, gates, params, pauli=pauli, method="shift")
+    assert np.max(np.abs(want)) > 1e-2
+    for dtype in ("c128", "c64"):
+        work = qs.State(n, dtype)
+        val, grad = qs.adjoint_grad(work, gates, params, pauli=pauli)
+        assert np.max(np.abs(grad - want)) < GTOL[dtype], dtype
+
+
+def test_autograd_function_matches():
+    n = 8
+    gates, params = W.ansatz_circuit(n, 4, seed=12)
+    work = qs.State(n, "c128")
+    p = torch.tensor(params, dtype=torch.float64, requires_grad=True)
+    E = qs.AdjointExpectation.apply(p, work, gates, "Z" + "I" * (n - 1), None)
+    (2.0 * E).backward()
+    want = oracle.gradient(n, gates, params, pauli="Z" + "I" * (n - 1), method="shift")
+    assert np.max(np.abs(p.grad.numpy() - 2.0 * want)) < 1e-9
+
+
+def test_adjoint_n26_full_size():
+    # the gradient workload at full size: n = 26, 25 layers (1300 angles),
+    # complex64 state; observables <Z_0> and the fidelity to the noiseless
+    # output at deviated angles.  Sampled components are checked against the
+    # parameter-shift rule and central finite differences (h = 1e-4) of the
+    # complex128 GPU forward pass.
+    n = 26
+    gates, params = W.ansatz_circuit(n, 25, seed=2026)
+    x = perturbed(params, 0.02, 7)
+    pauli = "Z" + "I" * (n - 1)
+    work = qs.State(n, "c64")
+    ref64 = qs.State(n, "c64").init_basis(0).apply_circuit(gates)      # noiseless output
+    zval, zgrad = qs.adjoint_grad(work, gates, x, pauli=pauli)
+    fval, fgrad = qs.adjoint_grad(work, gates, x, ref=ref64)
+    assert zgrad.size == 1300 and fgrad.size == 1300
+    ref_np = ref64.to_numpy()
+    del work, ref64
+    torch.cuda.empty_cache()
+    s128 = qs.State(n, "c128")
+    r128 = qs.State(n, "c128").from_numpy(ref_np.astype(np.complex128))
+
+    def run(pv):
+        g2 = [W.Gate(g.kind, g.target, angles=(float(pv[g.param]),), param=g.param) if g.param >= 0 else g
+              for g in gates]
+        s128.init_basis(0).apply_circuit(g2)
+
+    def Z(pv):
+        run(pv)
+        return s128.expect(pauli)
+
+    def F(pv):
+        run(pv)
+        return abs(r128.inner(s128)) ** 2
+
+    assert abs(zval - Z(x)) < 1e-5
+    assert abs(fval - F(x)) < 1e-5
+    assert 0.5 < fval < 0.999
+    rs = W.rng(99)
+    for k in sorted(set([0, 1299, 650] + [int(v) for v in rs.integers(0, 1300, size=2)])):
+        for fn, grad, tol in ((F, fgrad, 2e-4), (Z, zgrad, 2e-5)):
+            pp, pm = x.copy(), x.copy()
+            pp[k] += 1e-4
+            pm[k] -= 1e-4
+            fd = (fn(pp) - fn(pm)) / 2e-4
+            pp[k] = x[k] + math.pi / 2
+            pm[k] = x[k] - math.pi / 2
+            shift = (fn(pp) - fn(pm)) / 2
+            assert abs(fd - shift) < 1e-6, (k, fd, shift)
+            assert abs(grad[k] - shift) < tol, (k, grad[k], shift)
