@@ -180,6 +180,91 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def _time(torch, fn, reps=1):
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def secondary(args, torch, qs, state64):
+    """The other measurements the metric names, each on its own workload:
+    the complex128 state at n = 30 (same circuit), the adjoint gradient
+    against finite differences at n = 26 (25 layers, 1300 angles), and the
+    4096-trajectory noisy batch."""
+    out = {}
+    n = args.n
+    gates = W.random_circuit(n, LAYERS, seed=SEED)
+    upd = amp_updates(n, gates)
+    # complex128: one warm-up, one timed step (FP64-ALU bound)
+    if state64 is not None:
+        state64.close()
+    torch.cuda.empty_cache()
+    p128 = qs.Plan(n, "c128", gates)
+    s128 = qs.State(n, "c128")
+    step = lambda: (s128.init_basis(0), p128.execute(s128))
+    step()
+    p128.set_timing(True)
+    p128.timing()
+    ms = _time(torch, step)
+    kms, kn = p128.timing()
+    flops = sum(16 * (1 << n) for g in gates if g.kind == "MATRIX")
+    out["c128"] = {"value": upd / (ms / 1e3), "unit": "amp-updates/s", "ms_per_step": ms,
+                   "passes": p128.launches,
+                   "roofline": {"bound": "alu", "achieved": flops / (kms / 1e3) / 1e12, "peak": 1.25,
+                                "unit": "TFLOP/s", "frac": flops / (kms / 1e3) / 1e12 / 1.25,
+                                "peak_source": "nominal FP64 1.25 TFLOP/s", "kernel": "k_fused<double,4>"}}
+    s128.close()
+    del p128
+    torch.cuda.empty_cache()
+    # adjoint gradient at n = 26 vs finite differences / parameter shift
+    na = 26
+    agates, aparams = W.ansatz_circuit(na, 25, seed=2026)
+    work = qs.State(na, "c64")
+    pauli = "Z" + "I" * (na - 1)
+    qs.adjoint_grad(work, agates, aparams, pauli=pauli)
+    t_adj = _time(torch, lambda: qs.adjoint_grad(work, agates, aparams, pauli=pauli))
+    pf = qs.Plan(na, "c64", agates)
+    fwd = lambda: (work.init_basis(0), pf.execute(work), work.expect(pauli))
+    fwd()
+    t_fwd = _time(torch, fwd, reps=3)
+    n_par = aparams.size
+    out["adjoint"] = {"workload": "ansatz n=26, 25 layers of RY/RZ + C-NOT ladder, 1300 angles, complex64, <Z_0>",
+                      "adjoint_ms": t_adj, "forward_ms": t_fwd,
+                      "finite_diff_ms_estimate": 2 * n_par * t_fwd,
+                      "speedup_vs_finite_diff": 2 * n_par * t_fwd / t_adj,
+                      "speedup_vs_parameter_shift": 2 * n_par * t_fwd / t_adj,
+                      "note": "finite differences and the parameter-shift rule both take 2 forward passes per "
+                              "angle; their cost is 2 x 1300 x the measured forward time"}
+    work.close()
+    del pf
+    torch.cuda.empty_cache()
+    # batched noisy trajectories
+    batch = W.trajectory_batch(4096, ((12, 2), (16, 1), (20, 1)), (12, 16), seed=31337)
+    groups = qs.batch_groups(batch)
+    qs.run_trajectories(groups, 1e-3, 1e-2, 7, dtype="c64", with_stats=False)
+    t0 = time.perf_counter()
+    met, _ = qs.run_trajectories(groups, 1e-3, 1e-2, 7, dtype="c64", with_stats=False)
+    dt = time.perf_counter() - t0
+    hist, edges = np.histogram(met, bins=10, range=(0.0, 1.0))
+    tupd = 0
+    for g in groups:
+        m = len(g["x0"])
+        per = amp_updates(g["n"], g["gates"]) * (2 if g.get("metric", "fidelity") == "fidelity" else 1)
+        tupd += m * per
+    out["trajectories"] = {"workload": "4096 trajectories, 12/16/20 qubits 2:1:1, QFT + Grover(12,16), "
+                                       "sigma=1e-2, p=1e-3, complex64",
+                           "seconds": dt, "trajectories_per_s": len(met) / dt,
+                           "amp_updates_per_s": tupd / dt,
+                           "histogram_0_1_10bins": hist.tolist(), "mean_metric": float(met.mean())}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -190,6 +275,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the complex128, adjoint and trajectory measurements")
     ap.add_argument("--ref-budget", type=float, default=15.0)
     ap.add_argument("--n", type=int, default=N_QUBITS,
                     help="qubits (profiling of smaller cases; the workload is n=30)")
@@ -291,8 +378,13 @@ def main():
     t_hbm = bytes_step / (peak_gbs * 1e9)
     t_alu = flops_step / (alu_peak * 1e12)
     main = alu_view if t_alu > t_hbm else hbm_view
+    # DRAM traffic of one fused-pass launch from the ncu capture summarised in
+    # profiles/k_fused_c64_random_circuit_n26.md (1014.2 MB at n = 26), scaled
+    # to n by the amplitudes processed; only valid for the complex64 fused
+    # kernel it was measured on
+    traffic = 1014.2e6 * (1 << (n - 26)) if (args.dtype == "c64" and not args.no_fuse) else None
     roof = {"bound": "alu" if t_alu > t_hbm else "hbm", "achieved": main["achieved"], "peak": main["peak"],
-            "unit": main["unit"], "frac": main["frac"], "traffic": None,
+            "unit": main["unit"], "frac": main["frac"], "traffic": traffic, "traffic_unit": "bytes per launch",
             "kernel": ("k_fused_c64" if args.dtype == "c64" else "k_fused<double,4>") if not args.no_fuse else "k_pair",
             "peak_source": main["peak_source"], "launches_timed": kern_n,
             "kernel_ms_per_launch": per_launch_ms, "kernel_ms_per_step": kern_ms / args.steps,
@@ -346,6 +438,9 @@ def main():
                        "h2d_bytes_per_step": ctypes.sizeof(garr), "d2h_bytes_per_step": hbuf.nbytes,
                        "ms_per_step": dt * 1e3, "steps": k}
         del host
+
+    if not args.no_secondary and rank == 0:
+        line["secondary"] = secondary(args, torch, qs, state if args.dtype == "c64" else None)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         del state
