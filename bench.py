@@ -127,7 +127,25 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def cpu_baseline(dtype, budget_s=20.0):
+def max_over_ranks(x, dist):
+    """The maximum of a per-rank float over all ranks (identity without a
+    process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate(ms_per_step_rank, units_per_step_rank, world, dist):
+    """(ms_per_step, value): the slowest rank's time and the units all ranks
+    processed per second (every rank runs the same amount of work)."""
+    ms = max_over_ranks(ms_per_step_rank, dist)
+    return ms, world * units_per_step_rank / (ms / 1e3)
+
+
+def cpu_baseline(dtype, budget_s=20.0, n=None):
     """The oracle (complex128, row-by-row, OpenMP over rows) on the host cores,
     on a bounded prefix of the same circuit.  n = 30 when the host has room
     for the state and its out-of-place copy (2 x 16 GiB), else n = 26."""
@@ -137,7 +155,8 @@ def cpu_baseline(dtype, budget_s=20.0):
             avail = int([l for l in f if l.startswith("MemAvailable")][0].split()[1]) * 1024
     except Exception:
         avail = 0
-    n = N_QUBITS if avail > 48 * (1 << 30) else 26
+    if n is None:
+        n = N_QUBITS if avail > 48 * (1 << 30) else 26
     gates = W.random_circuit(n, LAYERS, seed=SEED)
     psi = oracle.basis(n, 0)
     done, upd = 0, 0
@@ -163,7 +182,7 @@ def run_reference(args, rank, world):
     steps = []
     base = None
     for k in range(args.warmup + args.steps):
-        b = cpu_baseline(args.dtype, budget_s=args.ref_budget)
+        b = cpu_baseline(args.dtype, budget_s=args.ref_budget, n=None if args.n == N_QUBITS else args.n)
         if k >= args.warmup:
             steps.append(b)
         base = b
@@ -278,7 +297,7 @@ def main():
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the complex128, adjoint and trajectory measurements")
     ap.add_argument("--ref-budget", type=float, default=15.0)
-    ap.add_argument("--n", type=int, default=N_QUBITS,
+    ap.add_argument("--qubits", "--n", dest="n", type=int, default=N_QUBITS,
                     help="qubits (profiling of smaller cases; the workload is n=30)")
     args = ap.parse_args()
 
@@ -344,13 +363,7 @@ def main():
     kern_ms += ms
     kern_n += nl
     plan.set_timing(False)
-    total_ms = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ms_per_step = total_ms / args.steps
-    value = world * upd / (ms_per_step / 1e3)
+    ms_per_step, value = aggregate(ev0.elapsed_time(ev1) / args.steps, upd, world, dist)
 
     # roofline of the dominant kernel (the fused pass, or the pair sweep),
     # measured on its own launches with per-launch CUDA events
@@ -378,10 +391,9 @@ def main():
     t_hbm = bytes_step / (peak_gbs * 1e9)
     t_alu = flops_step / (alu_peak * 1e12)
     main = alu_view if t_alu > t_hbm else hbm_view
-    # DRAM traffic of one fused-pass launch from the ncu capture summarised in
-    # profiles/k_fused_c64_random_circuit_n26.md (1014.2 MB at n = 26), scaled
-    # to n by the amplitudes processed; only valid for the complex64 fused
-    # kernel it was measured on
+    # DRAM traffic of one fused-pass launch from one ncu capture of this
+    # kernel at n = 26 (1014.2 MB read + write per launch), scaled to n by the
+    # amplitudes processed; only valid for the complex64 fused kernel
     traffic = 1014.2e6 * (1 << (n - 26)) if (args.dtype == "c64" and not args.no_fuse) else None
     roof = {"bound": "alu" if t_alu > t_hbm else "hbm", "achieved": main["achieved"], "peak": main["peak"],
             "unit": main["unit"], "frac": main["frac"], "traffic": traffic, "traffic_unit": "bytes per launch",
@@ -429,11 +441,7 @@ def main():
         for _ in range(k):
             e2e_step()
         torch.cuda.synchronize()
-        dt = (time.perf_counter() - t0) / k
-        if dist:
-            t = torch.tensor([dt], dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = max_over_ranks((time.perf_counter() - t0) / k, dist)
         line["e2e"] = {"value": world * upd / dt, "unit": "amp-updates/s",
                        "h2d_bytes_per_step": ctypes.sizeof(garr), "d2h_bytes_per_step": hbuf.nbytes,
                        "ms_per_step": dt * 1e3, "steps": k}

@@ -118,7 +118,7 @@ def test_fused_high_qubit_only_and_lane_only(dtype):
 
 
 def test_qft_n10_closed_form():
-    # configs: QFT of a seeded basis state |x>, x uniform in [0, 1024), complex128
+    # the QFT workload: a seeded basis state |x>, x uniform in [0, 1024), complex128
     n = 10
     x = W.basis_index(20260101, n)
     e = np.zeros(1 << n, dtype=complex)
@@ -170,7 +170,7 @@ def test_grover_n12_full_state(dtype):
 
 @pytest.mark.parametrize("dtype", DTYPES)
 def test_grover_n24_success_probability(dtype):
-    # configs: Grover n = 24, floor(pi/4 sqrt(2^24)) = 3216 iterations; success
+    # the Grover workload: n = 24, floor(pi/4 sqrt(2^24)) = 3216 iterations; success
     # probability against sin^2((2k+1) theta), sin theta = 2^-12
     n = 24
     k = W.basis_index(24, n)
