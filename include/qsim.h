@@ -220,6 +220,16 @@ qs_status qs_norm(qs_state *s, double *out);
 /* Divides the state by the square root of its (double precision) norm. */
 qs_status qs_renormalize(qs_state *s);
 
+/* Measurement gate (Sec. 2.2.3), one outcome per random number: out[k] is the
+ * index i with sum_{j<i} |alpha_j|^2 <= r[k] < sum_{j<=i} |alpha_j|^2, sums
+ * in double precision (chunked; a sequential sum can differ from it by
+ * rounding, which matters only when r[k] lies within that rounding of a
+ * boundary).  An r at or beyond the total (rounding) gives the last index
+ * with non-zero probability.  r: `shots` host doubles in [0, 1), else
+ * QS_EINVAL; out: `shots` host indices.  The state is not collapsed.
+ * At most 2^26 shots per call (QS_ERANGE).  Synchronous. */
+qs_status qs_measure(qs_state *s, const double *r, size_t shots, uint64_t *out);
+
 /* Norm of a state without any allocation, for callers that cannot allocate
  * device memory at the point they need it (a framework that owns the whole
  * device memory budget through its own pool, a latency-critical loop in which

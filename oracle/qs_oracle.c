@@ -330,12 +330,17 @@ uint64_t or_measure(const double *psi, int n, double r)
 {
     const uint64_t N = (uint64_t)1 << n;
     double c = 0.0;
+    uint64_t last = 0;
     for (uint64_t i = 0; i < N; i++) {
-        double next = c + psi[2 * i] * psi[2 * i] + psi[2 * i + 1] * psi[2 * i + 1];
+        double p = psi[2 * i] * psi[2 * i] + psi[2 * i + 1] * psi[2 * i + 1];
+        double next = c + p;
         if (c <= r && r < next) return i;
+        if (p > 0.0) last = i;
         c = next;
     }
-    return N - 1;   /* r beyond the rounded total: last index */
+    /* r at or beyond the rounded total: no interval contains it; the outcome
+     * is the last index whose interval is not empty */
+    return last;
 }
 
 /* ------------------------------------------------------------------------- */

@@ -110,6 +110,8 @@ _SIGS = {
     "qs_inner": [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(C128)],
     "qs_norm": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)],
     "qs_renormalize": [ctypes.c_void_p],
+    "qs_measure": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_size_t,
+                   ctypes.POINTER(ctypes.c_uint64)],
     "qs_norm_noalloc": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p],
     "qs_run_trajectories": [ctypes.POINTER(QsTrajGroup), ctypes.c_int, ctypes.POINTER(QsNoise), ctypes.c_uint64,
                             ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)],
@@ -288,6 +290,14 @@ class State:
     def renormalize(self):
         check(lib().qs_renormalize(self._h))
         return self
+
+    def measure(self, r) -> np.ndarray:
+        """Outcomes of the measurement gate for the random numbers r in [0, 1)."""
+        rr = np.ascontiguousarray(np.asarray(r, dtype=np.float64).reshape(-1))
+        out = np.zeros(max(1, rr.size), dtype=np.uint64)
+        check(lib().qs_measure(self._h, rr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), rr.size,
+                               out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))))
+        return out[:rr.size]
 
     # host copies
     def to_numpy(self) -> np.ndarray:

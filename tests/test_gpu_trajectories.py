@@ -140,3 +140,22 @@ def test_batch_4096_mixed_widths():
                                  g.get("metric", "fidelity"), g.get("target", 0))
             assert list(s) == [int(v) for v in st[t]], (k, i)
             assert abs(m - met[t]) < 5e-4, (k, i, m, met[t])
+
+
+@pytest.mark.parametrize("mode,p,sigma", [(qs.NOISE_DEPOLARIZING, 1e-3, 0.0), (qs.NOISE_FLIPS, 0.0, 0.03)])
+def test_paper_ht_experiment_n20(mode, p, sigma):
+    # the paper's experiment (Sec. 4.3.1) at its size: a 20-qubit register in
+    # |0...0>, the Hadamard transform applied k times (even), decoherence once
+    # per transform (depolarizing) or deviated H angles, averaged over runs;
+    # the |0><0| term against the paper's closed forms
+    n, k, T = 20, 10, 1024
+    gates = W.noisy_synthesis(W.hadamard_layer(n) * k)
+    met, _ = qs.run_trajectories([{"n": n, "gates": gates, "x0": np.zeros(T, np.uint64), "first": 0,
+                                   "metric": "prob", "target": 0}], p, sigma, seed=1000 + k, dtype="c64",
+                                 mode=mode, every=n, with_stats=False)
+    if p > 0:
+        want = ((1 + (1 - 4 * p / 3) ** k) / 2) ** n
+    else:
+        want = ((1 + math.exp(-9 * sigma ** 2 * k / 4)) / 2) ** n
+    se = met.std() / math.sqrt(T)
+    assert abs(met.mean() - want) < 4 * se + 2e-3, (met.mean(), want, se)

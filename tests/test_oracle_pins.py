@@ -238,6 +238,20 @@ def test_measurement_rule():
     cdf = np.cumsum(np.abs(psi) ** 2)
     for u in r.uniform(0, 0.999, size=200):
         assert oracle.measure(psi, u) == int(np.searchsorted(cdf, u, side="right"))
+    # zero-probability amplitudes are never an outcome; r at or beyond the
+    # rounded total gives the last index with non-zero probability
+    phi = psi.copy()
+    phi[5] = 0
+    phi[-3:] = 0
+    phi /= np.linalg.norm(phi)
+    cdf = np.cumsum(np.abs(phi) ** 2)
+    for u in np.concatenate([r.uniform(0, 0.999, size=200), [cdf[4], cdf[-1], 0.9999999999999999]]):
+        got = oracle.measure(phi, u)
+        if u < cdf[-1]:
+            assert got == int(np.searchsorted(cdf, u, side="right"))
+        else:
+            assert got == (1 << n) - 4
+        assert abs(phi[got]) > 0
 
 
 # ---------------------------------------------------------------------------
