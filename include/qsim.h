@@ -276,6 +276,20 @@ typedef struct {
 } qs_noise;
 
 enum { QS_NOISE_FLIPS = 0, QS_NOISE_DEPOLARIZING = 1 };
+
+/* Execution options of qs_run_trajectories (NULL: defaults).
+ *   no_fusion         1: one launch per gate step with the flips applied to
+ *                     the states (the plain batched path); 0 (default): for
+ *                     complex64 groups of 10 qubits or more, fused passes over
+ *                     all trajectories, the flips carried as a Pauli frame per
+ *                     trajectory and folded into the later gates
+ *   max_ops_per_pass  fusion depth of the fused path; 0: chosen by timing a
+ *                     few candidate depths on a small batch (cached per shape) */
+typedef struct {
+    int32_t no_fusion;
+    int32_t max_ops_per_pass;
+    int32_t reserved[6];
+} qs_traj_opts;
 enum { QS_TRAJ_FIDELITY = 0, QS_TRAJ_PROB = 1 };
 
 /* A group of trajectories that run the same circuit on the same width.
@@ -312,9 +326,10 @@ typedef struct {
  * precision; draws and gate synthesis are in double precision.  Synchronous
  * (returns when the results are on the host).  Device memory: the states of
  * all trajectories of the largest group (count x 2^n amplitudes) plus
- * per-step tables; QS_ENOMEM if it cannot be allocated. */
+ * per-step tables; QS_ENOMEM if it cannot be allocated.  opts (may be NULL)
+ * selects the fused or the plain path and the fusion depth. */
 qs_status qs_run_trajectories(const qs_traj_group *groups, int n_groups, const qs_noise *noise, uint64_t seed,
-                              qs_dtype dt, double *metric, uint64_t *stats);
+                              qs_dtype dt, const qs_traj_opts *opts, double *metric, uint64_t *stats);
 
 /* --------------------------------------------------------------------- */
 /* Gradients by the adjoint (reverse) sweep                                */

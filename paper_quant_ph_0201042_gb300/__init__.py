@@ -114,7 +114,8 @@ _SIGS = {
                    ctypes.POINTER(ctypes.c_uint64)],
     "qs_norm_noalloc": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p],
     "qs_run_trajectories": [ctypes.POINTER(QsTrajGroup), ctypes.c_int, ctypes.POINTER(QsNoise), ctypes.c_uint64,
-                            ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)],
+                            ctypes.c_int, ctypes.POINTER(QsExecOpts), ctypes.POINTER(ctypes.c_double),
+                            ctypes.POINTER(ctypes.c_uint64)],
     "qs_adjoint_grad": [ctypes.c_void_p, ctypes.POINTER(QsGate), ctypes.c_size_t, ctypes.POINTER(ctypes.c_double),
                         ctypes.c_size_t, ctypes.POINTER(QsObservable), ctypes.POINTER(ctypes.c_double),
                         ctypes.POINTER(ctypes.c_double)],
@@ -364,7 +365,8 @@ class Plan:
 
 
 def run_trajectories(groups: Sequence, p: float, sigma: float, seed: int, dtype: str = "c64",
-                     mode: int = NOISE_FLIPS, every: int = 1, with_stats: bool = True):
+                     mode: int = NOISE_FLIPS, every: int = 1, with_stats: bool = True, fuse: bool = True,
+                     max_ops: int = 0):
     """Runs batches of noisy trajectories (qs_run_trajectories).
 
     groups: sequence of dicts with keys n, gates, x0 (array of basis indices),
@@ -391,7 +393,8 @@ def run_trajectories(groups: Sequence, p: float, sigma: float, seed: int, dtype:
     nz = QsNoise(p, sigma, mode, every)
     met = np.zeros(max(1, total), dtype=np.float64)
     st = np.zeros((max(1, total), 4), dtype=np.uint64) if with_stats else None
-    check(lib().qs_run_trajectories(arr, len(groups), ctypes.byref(nz), seed, DTYPES[dtype],
+    opts = _opts(fuse, max_ops)   # same layout as qs_traj_opts
+    check(lib().qs_run_trajectories(arr, len(groups), ctypes.byref(nz), seed, DTYPES[dtype], ctypes.byref(opts),
                                     met.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                     st.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)) if st is not None else None))
     return met[:total], (st[:total] if st is not None else None)

@@ -408,7 +408,12 @@ struct PassC64 {
     uint64_t tiles;
     int32_t K, WB, nops, has_xpose;
     float scale;
-    int32_t pad;
+    int32_t n;                         // qubits (trajectory mode: state stride 2^n)
+    // trajectory mode: per-(trajectory, op) records; trajectory b's record of
+    // op k of this pass is recs[b * rec_stride + rec_off + k]
+    const TrajRec *recs;
+    uint64_t tiles_per_traj;
+    uint32_t rec_stride, rec_off;
     uint8_t tile_pos[24];
     uint64_t ld_reg[32], ld_warp[4];   // global offsets of register index j / warp bit w (first layout)
     uint64_t st_reg[32], st_warp[4];   // the same for the last layout (store)
@@ -492,12 +497,19 @@ __device__ __forceinline__ void s_reg_op(float2 (&v)[NA], int cls, uint32_t &xm,
     else s_gen<T, false, NA>(v, m, xm, rm, rv);
 }
 
-__global__ void __launch_bounds__(32 << QS_WB64, QS_FUSED_MINBLOCKS) k_fused_c64(float2 *__restrict__ a,
+// TRAJ: trajectory mode.  Tiles run over (trajectory, tile of its state);
+// each op takes its matrix and the XOR of its control values from the
+// trajectory's records, loaded into shared memory when the tile's trajectory
+// changes.
+template <bool TRAJ>
+__global__ void __launch_bounds__(32 << QS_WB64, QS_FUSED_MINBLOCKS) k_fused_c64(float2 *__restrict__ a0,
                                                                        const __grid_constant__ PassC64 P) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int K = P.K, WB = P.WB, nops = P.nops;
     float2 *sm = reinterpret_cast<float2 *>(smraw);
     POp *sops = reinterpret_cast<POp *>(smraw + (P.has_xpose ? (size_t(8) << K) : 0));
+    TrajRec *srec = reinterpret_cast<TrajRec *>(reinterpret_cast<unsigned char *>(sops) + size_t(nops) * sizeof(POp));
+    uint64_t cur_b = ~uint64_t(0);
     {
         const uint4 *src = reinterpret_cast<const uint4 *>(P.ops);
         uint4 *dst = reinterpret_cast<uint4 *>(sops);
@@ -513,8 +525,32 @@ __global__ void __launch_bounds__(32 << QS_WB64, QS_FUSED_MINBLOCKS) k_fused_c64
     for (int w = 0; w < WB64; ++w)
         if ((warp >> w) & 1) { ld_t += P.ld_warp[w]; st_t += P.st_warp[w]; }
 
-    for (uint64_t tile = blockIdx.x; tile < P.tiles; tile += gridDim.x) {
+    // trajectory mode walks a contiguous range of tiles per CTA, so that the
+    // tiles of one trajectory share one load of its op records
+    uint64_t t_begin = blockIdx.x, t_end = P.tiles, t_step = gridDim.x;
+    if (TRAJ) {
+        const uint64_t per = (P.tiles + gridDim.x - 1) / gridDim.x;
+        t_begin = uint64_t(blockIdx.x) * per;
+        t_end = t_begin + per < P.tiles ? t_begin + per : P.tiles;
+        t_step = 1;
+    }
+    for (uint64_t tile = t_begin; tile < t_end; tile += t_step) {
+        float2 *a = a0;
         uint64_t base = tile;
+        if (TRAJ) {
+            const uint64_t b = tile / P.tiles_per_traj;
+            base = tile - b * P.tiles_per_traj;
+            a = a0 + (b << P.n);
+            if (b != cur_b) {   // this trajectory's op records
+                __syncthreads();
+                const uint4 *src = reinterpret_cast<const uint4 *>(P.recs + b * P.rec_stride + P.rec_off);
+                uint4 *dst = reinterpret_cast<uint4 *>(srec);
+                const int words = nops * int(sizeof(TrajRec) / 16);
+                for (int k = threadIdx.x; k < words; k += blockDim.x) dst[k] = src[k];
+                __syncthreads();
+                cur_b = b;
+            }
+        }
         for (int k = 0; k < K; ++k) {
             const uint64_t low = (uint64_t(1) << P.tile_pos[k]) - 1;
             base = ((base & ~low) << 1) | (base & low);
@@ -559,18 +595,28 @@ __global__ void __launch_bounds__(32 << QS_WB64, QS_FUSED_MINBLOCKS) k_fused_c64
                 continue;
             }
             const uint64_t omask = uint64_t(oc.x) | (uint64_t(oc.y) << 32);
-            const uint64_t oval = uint64_t(oc.z) | (uint64_t(oc.w) << 32);
-            const bool ok = ((tl & tm) == tv) && ((base & omask) == oval);
-            const float4 c0 = reinterpret_cast<const float4 *>(q)[2], c1 = reinterpret_cast<const float4 *>(q)[3];
+            uint64_t oval = uint64_t(oc.z) | (uint64_t(oc.w) << 32);
+            float4 c0 = reinterpret_cast<const float4 *>(q)[2], c1 = reinterpret_cast<const float4 *>(q)[3];
+            uint32_t tvv = tv;
+            int rv2 = rv;
+            if (TRAJ) {
+                const TrajRec &tr = srec[k];
+                c0 = reinterpret_cast<const float4 *>(tr.u)[0];
+                c1 = reinterpret_cast<const float4 *>(tr.u)[1];
+                oval ^= tr.ovx;
+                tvv ^= tr.tvx;
+                rv2 ^= tr.rvx;
+            }
+            const bool ok = ((tl & tm) == tvv) && ((base & omask) == oval);
             const Mat4<float> mt = {make_float2(c0.x, c0.y), make_float2(c0.z, c0.w), make_float2(c1.x, c1.y),
                                     make_float2(c1.z, c1.w)};
             if (type == OP_REG) {
                 const bool lc = (tm & 31u) != 0;
-                if (tpos == 0) s_reg_op<0, NA>(v, cls, xm, ok, rm, rv, lc, mt);
-                else if (tpos == 1) s_reg_op<1, NA>(v, cls, xm, ok, rm, rv, lc, mt);
-                else if (tpos == 2) s_reg_op<2, NA>(v, cls, xm, ok, rm, rv, lc, mt);
-                else if (tpos == 3) s_reg_op<3, NA>(v, cls, xm, ok, rm, rv, lc, mt);
-                else s_reg_op<(RB64 > 4 ? 4 : 0), NA>(v, cls, xm, ok, rm, rv, lc, mt);
+                if (tpos == 0) s_reg_op<0, NA>(v, cls, xm, ok, rm, rv2, lc, mt);
+                else if (tpos == 1) s_reg_op<1, NA>(v, cls, xm, ok, rm, rv2, lc, mt);
+                else if (tpos == 2) s_reg_op<2, NA>(v, cls, xm, ok, rm, rv2, lc, mt);
+                else if (tpos == 3) s_reg_op<3, NA>(v, cls, xm, ok, rm, rv2, lc, mt);
+                else s_reg_op<(RB64 > 4 ? 4 : 0), NA>(v, cls, xm, ok, rm, rv2, lc, mt);
             } else if (type == OP_LANE) {
                 const int m = 1 << tpos;
                 const bool hi = (lane >> tpos) & 1;
@@ -584,7 +630,7 @@ __global__ void __launch_bounds__(32 << QS_WB64, QS_FUSED_MINBLOCKS) k_fused_c64
 #pragma unroll
                     for (int j = 0; j < NA; ++j) {
                         const float2 o = shfl<float>(v[j], m);
-                        if (ok && lpred(j, xm, rm, rv)) v[j] = o;
+                        if (ok && lpred(j, xm, rm, rv2)) v[j] = o;
                     }
                 } else {
                     const float2 cs = hi ? mt.u11 : mt.u00, co = hi ? mt.u10 : mt.u01;
@@ -598,7 +644,7 @@ __global__ void __launch_bounds__(32 << QS_WB64, QS_FUSED_MINBLOCKS) k_fused_c64
 #pragma unroll
                         for (int j = 0; j < NA; ++j) {
                             const float2 o = shfl<float>(v[j], m);
-                            if (ok && lpred(j, xm, rm, rv)) v[j] = cmad2<float>(cs, v[j], co, o);
+                            if (ok && lpred(j, xm, rm, rv2)) v[j] = cmad2<float>(cs, v[j], co, o);
                         }
                     }
                 }
@@ -606,17 +652,17 @@ __global__ void __launch_bounds__(32 << QS_WB64, QS_FUSED_MINBLOCKS) k_fused_c64
                 if (!ok) continue;
                 const float2 d0 = mt.u00, d1 = mt.u01;
                 if (tsel == 0) {
-                    if (tpos == 0) s_diag<0, NA>(v, d0, d1, xm, rm, rv);
-                    else if (tpos == 1) s_diag<1, NA>(v, d0, d1, xm, rm, rv);
-                    else if (tpos == 2) s_diag<2, NA>(v, d0, d1, xm, rm, rv);
-                    else if (tpos == 3) s_diag<3, NA>(v, d0, d1, xm, rm, rv);
-                    else s_diag<(RB64 > 4 ? 4 : 0), NA>(v, d0, d1, xm, rm, rv);
+                    if (tpos == 0) s_diag<0, NA>(v, d0, d1, xm, rm, rv2);
+                    else if (tpos == 1) s_diag<1, NA>(v, d0, d1, xm, rm, rv2);
+                    else if (tpos == 2) s_diag<2, NA>(v, d0, d1, xm, rm, rv2);
+                    else if (tpos == 3) s_diag<3, NA>(v, d0, d1, xm, rm, rv2);
+                    else s_diag<(RB64 > 4 ? 4 : 0), NA>(v, d0, d1, xm, rm, rv2);
                 } else {
                     const uint64_t word = tsel == 1 ? uint64_t(tl) : base;
                     const float2 d = ((word >> tpos) & 1) ? d1 : d0;
 #pragma unroll
                     for (int j = 0; j < NA; ++j)
-                        if (lpred(j, xm, rm, rv)) v[j] = cmul<float>(d, v[j]);
+                        if (lpred(j, xm, rm, rv2)) v[j] = cmul<float>(d, v[j]);
                 }
             }
         }
@@ -742,7 +788,7 @@ uint32_t pack_layout(const std::vector<int> &regs, const std::vector<int> &warps
 
 template <typename R>
 qs_status resolve_pass(int n, int RB, int WB, const PlannedPass &pp, PassDesc<R> &D,
-                       std::vector<FOp<R>> &ops_out) {
+                       std::vector<FOp<R>> &ops_out, std::vector<TrajOpMeta> *metas = nullptr) {
     const int H = RB + WB;
     std::memset(&D, 0, sizeof(D));
     D.K = LB + H;
@@ -784,10 +830,17 @@ qs_status resolve_pass(int n, int RB, int WB, const PlannedPass &pp, PassDesc<R>
     D.lay0 = pack_layout(regs, warps);
 
     ops_out.clear();
+    if (metas) metas->clear();
     int n_hb = 0;
+    TrajOpMeta cur_meta{};
     auto push = [&](const FOp<R> &f) -> bool {
         if (int(ops_out.size()) >= MAX_OPS) return false;
         ops_out.push_back(f);
+        if (metas) {
+            TrajOpMeta m = cur_meta;
+            if (f.type == OP_XPOSE) m.step = -1;
+            metas->push_back(m);
+        }
         return true;
     };
     for (size_t k = 0; k < m; ++k) {
@@ -816,6 +869,15 @@ qs_status resolve_pass(int n, int RB, int WB, const PlannedPass &pp, PassDesc<R>
             if (!push(x)) return QS_EUNSUPPORTED;
         }
         FOp<R> f{};
+        cur_meta = TrajOpMeta{};
+        cur_meta.step = o.step;
+        cur_meta.msrc = o.msrc;
+        cur_meta.tbit = o.bit;
+        cur_meta.diag = is_diag(o.cls) ? 1 : 0;
+        cur_meta.cmask = o.cmask;
+        for (int k2 = 0; k2 < 8; ++k2) cur_meta.u[k2] = o.u[k2];
+        for (int k2 = 0; k2 < 8; ++k2) cur_meta.reg_src[k2] = -1;
+        for (int k2 = 0; k2 < 16; ++k2) cur_meta.thr_src[k2] = -1;
         // controls
         for (int b = 0; b < n; ++b) {
             if (!((o.cmask >> b) & 1)) continue;
@@ -823,6 +885,7 @@ qs_status resolve_pass(int n, int RB, int WB, const PlannedPass &pp, PassDesc<R>
             if (b < LB) {
                 f.tmask |= uint16_t(1u << b);
                 if (val) f.tval |= uint16_t(1u << b);
+                cur_meta.thr_src[b] = int8_t(b);
             } else if (hidx.count(b)) {
                 const int i = hidx[b];
                 auto it = std::find(regs.begin(), regs.end(), i);
@@ -830,16 +893,19 @@ qs_status resolve_pass(int n, int RB, int WB, const PlannedPass &pp, PassDesc<R>
                     const int r = int(it - regs.begin());
                     f.rmask |= uint8_t(1u << r);
                     if (val) f.rval |= uint8_t(1u << r);
+                    cur_meta.reg_src[r] = int8_t(b);
                 } else {
                     const int w = int(std::find(warps.begin(), warps.end(), i) - warps.begin());
                     f.tmask |= uint16_t(1u << (LB + w));
                     if (val) f.tval |= uint16_t(1u << (LB + w));
+                    cur_meta.thr_src[LB + w] = int8_t(b);
                 }
             } else {
                 f.omask |= uint64_t(1) << b;
                 if (val) f.oval |= uint64_t(1) << b;
             }
         }
+        cur_meta.omask = f.omask;
         if (is_diag(o.cls)) {
             f.type = OP_DIAG;
             // (d0, d1)
@@ -1121,9 +1187,9 @@ cudaError_t ensure_device_c64(Plan *P, cudaStream_t st) {
         int sms = 0, per_sm = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const size_t smem_max = (size_t(8) << (LB + RB64 + WB64)) + MAX_OPS * sizeof(POp);
-        e = cudaFuncSetAttribute(k_fused_c64, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_max));
+        e = cudaFuncSetAttribute(k_fused_c64<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_max));
         if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_c64, 32 << WB64, smem_max);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_c64<false>, 32 << WB64, smem_max);
         if (e != cudaSuccess) return e;
         g = std::max(1, sms * std::max(1, per_sm));
     }
@@ -1137,7 +1203,7 @@ cudaError_t run_passes_c64(qs_state *s, Plan *P) {
         const uint64_t grid = std::min<uint64_t>(D.tiles, uint64_t(P->grid));
         cudaError_t e = P->mark(s->stream, false);
         if (e != cudaSuccess) return e;
-        k_fused_c64<<<unsigned(grid), 32u << D.WB, smem, s->stream>>>(static_cast<float2 *>(s->d), D);
+        k_fused_c64<false><<<unsigned(grid), 32u << D.WB, smem, s->stream>>>(static_cast<float2 *>(s->d), D);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         e = P->mark(s->stream, true);
@@ -1277,5 +1343,96 @@ std::string plan_describe(const Plan *p) {
 
 int plan_n(const Plan *p) { return p->n; }
 qs_dtype plan_dtype(const Plan *p) { return p->dt; }
+
+// ---------------------------------------------------------------------------
+// Trajectory mode: a plan over one group's op list (SWAP-free, classes fixed
+// by the caller), executed on all trajectories of the group at once.
+// ---------------------------------------------------------------------------
+struct TrajPlan {
+    int n = 0;
+    std::vector<PassC64> pc;
+    std::vector<std::vector<POp>> tables;
+    std::vector<TrajOpMeta> metas;
+    void *dev_ops = nullptr;
+    int grid = 0;
+    ~TrajPlan() {
+        if (dev_ops) cudaFree(dev_ops);
+    }
+};
+
+qs_status traj_plan_build(int n, const std::vector<HostOp> &ops, int max_ops, TrajPlan **out) {
+    if (n < LB + RB64) return fail(QS_EUNSUPPORTED, "trajectory passes need n >= 10");
+    TrajPlan *T = new TrajPlan();
+    T->n = n;
+    const int WB = std::min(WB64, n - LB - RB64);
+    const int H = RB64 + WB;
+    max_ops = std::max(4, std::min(max_ops > 0 ? max_ops : MAX_OPS, MAX_OPS));
+    std::vector<PlannedPass> passes = form_passes(n, H, max_ops, ops);
+    for (const PlannedPass &pp : passes) {
+        PassDesc<float> D;
+        std::vector<FOp<float>> f;
+        std::vector<TrajOpMeta> m;
+        qs_status st = resolve_pass<float>(n, RB64, WB, pp, D, f, &m);
+        if (st != QS_OK) { delete T; return fail(st, "trajectory planner: pass too large"); }
+        D.tiles = uint64_t(1) << (n - D.K);
+        PassC64 c;
+        std::vector<POp> pops;
+        convert_c64(D, f, c, pops);
+        c.n = n;
+        c.rec_off = uint32_t(T->metas.size());
+        c.tiles_per_traj = D.tiles;
+        T->metas.insert(T->metas.end(), m.begin(), m.end());
+        T->pc.push_back(c);
+        T->tables.push_back(std::move(pops));
+    }
+    for (PassC64 &c : T->pc) c.rec_stride = uint32_t(T->metas.size());
+    // op tables on the device
+    std::vector<POp> flat;
+    std::vector<size_t> offs;
+    for (auto &t : T->tables) {
+        offs.push_back(flat.size());
+        flat.insert(flat.end(), t.begin(), t.end());
+    }
+    if (!flat.empty()) {
+        if (cudaMalloc(&T->dev_ops, flat.size() * sizeof(POp)) != cudaSuccess) {
+            cudaGetLastError();
+            delete T;
+            return fail(QS_ENOMEM, "trajectory planner: device allocation failed");
+        }
+        cudaError_t e = cudaMemcpy(T->dev_ops, flat.data(), flat.size() * sizeof(POp), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) { delete T; return cuda_fail(e, "trajectory planner upload"); }
+        for (size_t k = 0; k < T->pc.size(); ++k) T->pc[k].ops = static_cast<const POp *>(T->dev_ops) + offs[k];
+    }
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t smem_max = (size_t(8) << (LB + RB64 + WB64)) + MAX_OPS * (sizeof(POp) + sizeof(TrajRec));
+    cudaError_t e = cudaFuncSetAttribute(k_fused_c64<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_max));
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_c64<true>, 32 << WB64, smem_max);
+    if (e != cudaSuccess) { delete T; return cuda_fail(e, "trajectory planner: kernel attributes"); }
+    T->grid = std::max(1, sms * std::max(1, per_sm));
+    *out = T;
+    return QS_OK;
+}
+
+const std::vector<TrajOpMeta> &traj_plan_metas(const TrajPlan *p) { return p->metas; }
+int64_t traj_plan_launches(const TrajPlan *p) { return int64_t(p->pc.size()); }
+
+cudaError_t traj_plan_run(TrajPlan *T, float2 *states, uint32_t count, const TrajRec *recs, cudaStream_t st) {
+    for (const PassC64 &c0 : T->pc) {
+        PassC64 D = c0;
+        D.recs = recs;
+        D.tiles = D.tiles_per_traj * count;
+        const size_t smem = (D.has_xpose ? (size_t(8) << D.K) : 0) + size_t(D.nops) * (sizeof(POp) + sizeof(TrajRec));
+        const uint64_t grid = std::min<uint64_t>(D.tiles, uint64_t(T->grid));
+        k_fused_c64<true><<<unsigned(grid), 32u << D.WB, smem, st>>>(states, D);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+void traj_plan_destroy(TrajPlan *p) { delete p; }
 
 }  // namespace qs

@@ -77,6 +77,32 @@ struct HostOp {
     int32_t param;        // parameter index or -1 (differentiation)
     int32_t kind;         // original qs_gate_kind
     double theta[2];
+    int32_t step;         // trajectory mode: gate step whose noisy matrix and frame the op uses
+    int32_t msrc;         // trajectory mode: 0 noisy matrix of `step`, 1 the fixed matrix u
+};
+
+// Trajectory mode of the fused complex64 pass (qs_fused.cu / qs_traj.cu):
+// every trajectory of a group shares the pass structure; what differs per
+// trajectory is each op's matrix and control values, written per
+// (trajectory, op) into a TrajRec by a precompute kernel from TrajOpMeta.
+struct TrajOpMeta {
+    int32_t step;          // -1: a transpose (no record)
+    int32_t msrc;          // 0: the trajectory's noisy matrix of `step`; 1: the fixed matrix u
+    int32_t tbit;          // target index bit
+    int32_t diag;          // 1: diagonal op (u[0..1] = d0, u[6..7] = d1)
+    uint64_t cmask;        // control mask over index bits
+    uint64_t omask;        // the controls outside the tile
+    int8_t reg_src[8];     // index bit of the register-slot control r (or -1)
+    int8_t thr_src[16];    // index bit of the thread-bit control t (or -1)
+    double u[8];           // fixed matrix (msrc = 1)
+};
+
+struct TrajRec {           // per (trajectory, op): 48 bytes
+    float2 u[4];           // matrix (diagonal ops: d0 in u[0], d1 in u[1])
+    uint64_t ovx;          // XOR on the outer-bit control values
+    uint16_t tvx;          // XOR on the thread-bit control values
+    uint8_t rvx;           // XOR on the register-slot control values
+    uint8_t pad[5];
 };
 
 // Per-state scratch for reductions.
@@ -125,6 +151,13 @@ qs_status plan_timing(Plan *p, double *ms, int64_t *launches);
 void plan_destroy(Plan *p);
 void plan_counts(const Plan *p, int64_t *launches, int64_t *gates);
 int plan_n(const Plan *p);
+
+struct TrajPlan;
+qs_status traj_plan_build(int n, const std::vector<HostOp> &ops, int max_ops, TrajPlan **out);
+const std::vector<TrajOpMeta> &traj_plan_metas(const TrajPlan *p);
+int64_t traj_plan_launches(const TrajPlan *p);
+cudaError_t traj_plan_run(TrajPlan *p, float2 *states, uint32_t count, const TrajRec *recs, cudaStream_t st);
+void traj_plan_destroy(TrajPlan *p);
 std::string plan_describe(const Plan *p);
 qs_dtype plan_dtype(const Plan *p);
 

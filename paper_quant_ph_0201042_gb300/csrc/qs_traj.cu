@@ -25,6 +25,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "qs_internal.cuh"
@@ -346,9 +349,238 @@ struct DevBuf {
     cudaError_t alloc(size_t bytes) { return cudaMalloc(&p, std::max<size_t>(bytes, 16)); }
 };
 
+// ---------------------------------------------------------------------------
+// Fused trajectory path (complex64, n >= 10).  Flips are not applied to the
+// data: each trajectory carries a Pauli frame F (psi_true = F psi_sim, F an X
+// and a Z mask up to a phase, the XOR of all flips so far).  A later gate G is
+// applied as F^dagger G F: its target matrix conjugated by the frame's Pauli
+// on the target, its control values flipped where F has an X.  All
+// trajectories then share one fused pass structure; a precompute writes each
+// (trajectory, op) record, and the metric reads psi_sim at index ^ F_x.
+// ---------------------------------------------------------------------------
+
+// Frame before every step (and after the last) of every trajectory.
+__global__ void k_frames(const uint64_t *__restrict__ ftab, int m, uint32_t count, uint64_t *__restrict__ fb) {
+    for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < count; b += gridDim.x * blockDim.x) {
+        uint64_t fx = 0, fz = 0;
+        uint64_t *o = fb + uint64_t(b) * (m + 1) * 2;
+        for (int s = 0; s < m; ++s) {
+            o[2 * s] = fx;
+            o[2 * s + 1] = fz;
+            const uint64_t e = (uint64_t(b) * m + s) * 2;
+            fx ^= ftab[e];
+            fz ^= ftab[e + 1] & ~(uint64_t(3) << 62);
+        }
+        o[2 * m] = fx;
+        o[2 * m + 1] = fz;
+    }
+}
+
+// Per (trajectory, op) record: matrix conjugated by the frame's Pauli on the
+// target (F^dagger G F with F = X^x Z^z: first swap rows and columns for X,
+// then negate the off-diagonal for Z), control-value XORs where F has an X.
+__global__ void __launch_bounds__(THREADS) k_optab(const TrajOpMeta *__restrict__ metas, uint32_t nmeta,
+                                                   const float2 *__restrict__ mtab, int m, uint32_t count,
+                                                   const uint64_t *__restrict__ fb, TrajRec *__restrict__ recs) {
+    const uint64_t total = uint64_t(count) * nmeta;
+    for (uint64_t it = uint64_t(blockIdx.x) * THREADS + threadIdx.x; it < total; it += uint64_t(gridDim.x) * THREADS) {
+        const uint32_t b = uint32_t(it / nmeta), k = uint32_t(it % nmeta);
+        const TrajOpMeta &d = metas[k];
+        if (d.step < 0) continue;
+        const uint64_t fx = fb[(uint64_t(b) * (m + 1) + d.step) * 2];
+        const uint64_t fz = fb[(uint64_t(b) * (m + 1) + d.step) * 2 + 1];
+        float2 u[4];
+        if (d.msrc == 0) {
+            const float2 *src = mtab + (uint64_t(b) * m + d.step) * 4;
+            for (int e = 0; e < 4; ++e) u[e] = src[e];
+        } else {
+            for (int e = 0; e < 4; ++e) u[e] = make_float2(float(d.u[2 * e]), float(d.u[2 * e + 1]));
+        }
+        const bool px = (fx >> d.tbit) & 1, pz = (fz >> d.tbit) & 1;
+        TrajRec r;
+        if (d.diag) {
+            float2 d0 = u[0], d1 = u[3];
+            if (px) { const float2 t = d0; d0 = d1; d1 = t; }
+            r.u[0] = d0; r.u[1] = d1; r.u[2] = make_float2(0.f, 0.f); r.u[3] = make_float2(0.f, 0.f);
+        } else {
+            if (px) {
+                const float2 t0 = u[0], t1 = u[1];
+                u[0] = u[3]; u[1] = u[2]; u[2] = t1; u[3] = t0;
+            }
+            if (pz) {
+                u[1] = make_float2(-u[1].x, -u[1].y);
+                u[2] = make_float2(-u[2].x, -u[2].y);
+            }
+            for (int e = 0; e < 4; ++e) r.u[e] = u[e];
+        }
+        const uint64_t flip = fx & d.cmask;
+        uint8_t rvx = 0;
+        uint16_t tvx = 0;
+        for (int q = 0; q < 8; ++q)
+            if (d.reg_src[q] >= 0 && ((flip >> d.reg_src[q]) & 1)) rvx |= uint8_t(1u << q);
+        for (int q = 0; q < 16; ++q)
+            if (d.thr_src[q] >= 0 && ((flip >> d.thr_src[q]) & 1)) tvx |= uint16_t(1u << q);
+        r.ovx = flip & d.omask;
+        r.tvx = tvx;
+        r.rvx = rvx;
+        for (int q = 0; q < 5; ++q) r.pad[q] = 0;
+        recs[it] = r;
+    }
+}
+
 template <typename R>
-qs_status run_group(const qs_traj_group &g, const qs_noise &nz, uint64_t seed, double *metric, uint64_t *stats) {
+__global__ void k_metric_frame(const cplx<R> *__restrict__ st, int n, uint32_t count, const uint64_t *__restrict__ idx,
+                               uint64_t target, int use_idx, const uint64_t *__restrict__ fb, int m,
+                               double *__restrict__ out) {
+    for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < count; b += gridDim.x * blockDim.x) {
+        const uint64_t fx = fb[(uint64_t(b) * (m + 1) + m) * 2];
+        const uint64_t i = (use_idx ? idx[b] : target) ^ fx;
+        const cplx<R> v = st[(uint64_t(b) << n) + i];
+        const double x = double(v.x), y = double(v.y);
+        out[b] = x * x + y * y;
+    }
+}
+
+bool diag_kind(int kind) {
+    return kind == QS_GATE_UP1 || kind == QS_GATE_UP2 || kind == QS_GATE_RZ || kind == QS_GATE_Z;
+}
+
+// Op list of a group for the fused path: forward steps (noisy matrices), then
+// the inverse noiseless circuit for the fidelity echo (fixed matrices, final
+// frame).  SWAPs become three C-NOTs (fixed X matrices).
+void traj_ops(const std::vector<HostOp> &ops, bool echo, std::vector<HostOp> &out) {
+    const int m = int(ops.size());
+    auto add_swap = [&](const HostOp &o, int step) {
+        HostOp x{};
+        x.cls = GC_GEN;
+        x.kind = QS_GATE_MATRIX;
+        x.param = -1;
+        x.u[2] = 1.0; x.u[4] = 1.0;
+        x.step = step;
+        x.msrc = 1;
+        HostOp c1 = x, c2 = x;
+        c1.bit = o.bit; c1.cmask = uint64_t(1) << o.bit2; c1.cval = uint64_t(1) << o.bit2;
+        c2.bit = o.bit2; c2.cmask = o.cmask | (uint64_t(1) << o.bit); c2.cval = o.cval | (uint64_t(1) << o.bit);
+        out.push_back(c1);
+        out.push_back(c2);
+        out.push_back(c1);
+    };
+    for (int s = 0; s < m; ++s) {
+        const HostOp &o = ops[s];
+        if (o.cls == GC_SWAP) { add_swap(o, s); continue; }
+        HostOp q = o;
+        q.step = s;
+        q.msrc = 0;
+        const bool dg = diag_kind(o.kind) ||
+                        (o.kind == QS_GATE_MATRIX && (o.cls == GC_DIAG || o.cls == GC_PHASE || o.cls == GC_ID));
+        q.cls = dg ? GC_DIAG : GC_GEN;
+        q.kind = QS_GATE_MATRIX;   // no Hadamard folding: the matrices differ per trajectory
+        out.push_back(q);
+    }
+    if (!echo) return;
+    for (int s = m - 1; s >= 0; --s) {
+        const HostOp &o = ops[s];
+        if (o.cls == GC_SWAP) { add_swap(o, m); continue; }
+        HostOp q = o;
+        const double *u = o.u;
+        const double v[8] = {u[0], -u[1], u[4], -u[5], u[2], -u[3], u[6], -u[7]};   // U^dagger
+        for (int k = 0; k < 8; ++k) q.u[k] = v[k];
+        q.step = m;
+        q.msrc = 1;
+        const bool dg = diag_kind(o.kind) || o.cls == GC_DIAG || o.cls == GC_PHASE || o.cls == GC_ID;
+        q.cls = dg ? GC_DIAG : GC_GEN;
+        q.kind = QS_GATE_MATRIX;
+        out.push_back(q);
+    }
+}
+
+// Fusion depth of a group's fused passes, chosen by timing: every candidate
+// depth runs the group's passes on a sub-batch of its own trajectories (their
+// real op records), and the fastest is kept for that (width, op list, batch
+// size) on this device.
+uint64_t ops_hash(const std::vector<HostOp> &ops) {
+    uint64_t h = 1469598103934665603ull;
+    for (const HostOp &o : ops) {
+        const uint64_t v[5] = {uint64_t(o.cls), uint64_t(o.bit), o.cmask, o.cval, uint64_t(o.step)};
+        for (uint64_t x : v) { h ^= x; h *= 1099511628211ull; }
+    }
+    return h;
+}
+
+qs_status tune_depth(int n, const std::vector<HostOp> &fops, uint32_t count, int m, const float2 *mtab,
+                     const uint64_t *ftab, int *out) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, uint64_t, uint32_t>, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const uint32_t sub = std::min<uint32_t>(count, n >= 18 ? 16u : 128u);
+    const auto key = std::make_tuple(dev, n, ops_hash(fops), sub);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) { *out = it->second; return QS_OK; }
+    }
+    const int cands[3] = {120, 48, 16};
+    float best_ms = 1e30f;
+    int best = cands[0];
+    DevBuf st, fb, meta, recs;
+    const uint64_t N = uint64_t(1) << n;
+    if (st.alloc(sizeof(float2) * N * sub) != cudaSuccess || fb.alloc(sizeof(uint64_t) * 2 * uint64_t(sub) * (m + 1)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(QS_ENOMEM, "trajectory tuning: device allocation failed");
+    }
+    k_frames<<<grid_for(sub), THREADS>>>(ftab, m, sub, static_cast<uint64_t *>(fb.p));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int c : cands) {
+        TrajPlan *tp = nullptr;
+        qs_status rc = traj_plan_build(n, fops, c, &tp);
+        if (rc != QS_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
+        const std::vector<TrajOpMeta> &metas = traj_plan_metas(tp);
+        DevBuf dm, dr;
+        if (dm.alloc(sizeof(TrajOpMeta) * metas.size()) != cudaSuccess ||
+            dr.alloc(sizeof(TrajRec) * uint64_t(sub) * metas.size()) != cudaSuccess) {
+            cudaGetLastError();
+            traj_plan_destroy(tp);
+            cudaEventDestroy(e0); cudaEventDestroy(e1);
+            return fail(QS_ENOMEM, "trajectory tuning: device allocation failed");
+        }
+        cudaMemcpy(dm.p, metas.data(), sizeof(TrajOpMeta) * metas.size(), cudaMemcpyHostToDevice);
+        k_optab<<<grid_for(uint64_t(sub) * metas.size()), THREADS>>>(
+            static_cast<const TrajOpMeta *>(dm.p), uint32_t(metas.size()), mtab, m, sub,
+            static_cast<const uint64_t *>(fb.p), static_cast<TrajRec *>(dr.p));
+        cudaMemset(st.p, 0, sizeof(float2) * N * sub);
+        float ms = 0.f;
+        cudaError_t e = traj_plan_run(tp, static_cast<float2 *>(st.p), sub, static_cast<const TrajRec *>(dr.p), nullptr);
+        if (e == cudaSuccess) {
+            cudaEventRecord(e0);
+            e = traj_plan_run(tp, static_cast<float2 *>(st.p), sub, static_cast<const TrajRec *>(dr.p), nullptr);
+            cudaEventRecord(e1);
+        }
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        traj_plan_destroy(tp);
+        if (e != cudaSuccess) {
+            cudaEventDestroy(e0); cudaEventDestroy(e1);
+            return cuda_fail(e, "trajectory tuning");
+        }
+        if (ms < best_ms) { best_ms = ms; best = c; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::lock_guard<std::mutex> lk(mu);
+    cache[key] = best;
+    *out = best;
+    return QS_OK;
+}
+
+template <typename R>
+qs_status run_group(const qs_traj_group &g, const qs_noise &nz, uint64_t seed, double *metric, uint64_t *stats,
+                    int fuse_mode, int max_ops) {
     const int n = g.n;
+    // fused passes for complex64 registers of 10 qubits or more
+    const bool fused = fuse_mode != 0 && sizeof(R) == 4 && n >= 10;
     const int m = int(g.m);
     const uint32_t count = g.count;
     if (count == 0) return QS_OK;
@@ -411,6 +643,70 @@ qs_status run_group(const qs_traj_group &g, const qs_noise &nz, uint64_t seed, d
                                              static_cast<uint32_t *>(d_lists.p), static_cast<uint32_t *>(d_lens.p));
     }
     if ((st = ck(cudaGetLastError(), "trajectory launch")) != QS_OK) return st;
+    if (fused) {
+        // fused passes over all trajectories with per-trajectory op records
+        std::vector<HostOp> fops;
+        traj_ops(ops, g.metric == QS_TRAJ_FIDELITY, fops);
+        if ((st = ck(cudaDeviceSynchronize(), "trajectory noise")) != QS_OK) return st;
+        int depth = max_ops;
+        if (depth <= 0) {
+            st = tune_depth(n, fops, count, m, static_cast<const float2 *>(d_mtab.p),
+                            static_cast<const uint64_t *>(d_ftab.p), &depth);
+            if (st != QS_OK) return st;
+        }
+        TrajPlan *tp = nullptr;
+        if ((st = traj_plan_build(n, fops, depth, &tp)) != QS_OK) return st;
+        const std::vector<TrajOpMeta> &metas = traj_plan_metas(tp);
+        DevBuf d_fb, d_meta, d_recs;
+        if (d_fb.alloc(sizeof(uint64_t) * 2 * uint64_t(count) * (m + 1)) != cudaSuccess ||
+            d_meta.alloc(sizeof(TrajOpMeta) * std::max<size_t>(1, metas.size())) != cudaSuccess ||
+            d_recs.alloc(sizeof(TrajRec) * uint64_t(count) * std::max<size_t>(1, metas.size())) != cudaSuccess) {
+            cudaGetLastError();
+            traj_plan_destroy(tp);
+            return fail(QS_ENOMEM, "trajectory batch: device allocation failed");
+        }
+        st = ck(cudaMemcpy(d_meta.p, metas.data(), sizeof(TrajOpMeta) * metas.size(), cudaMemcpyHostToDevice), "upload");
+        if (st == QS_OK) {
+            // the whole group (frames, op records, every pass, metric) as one
+            // captured graph, launched once
+            cudaStream_t cs = nullptr;
+            cudaGraph_t graph = nullptr;
+            cudaGraphExec_t exec = nullptr;
+            cudaError_t e2 = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+            if (e2 == cudaSuccess) e2 = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+            if (e2 == cudaSuccess) {
+                k_frames<<<grid_for(count), THREADS, 0, cs>>>(static_cast<const uint64_t *>(d_ftab.p), m, count,
+                                                              static_cast<uint64_t *>(d_fb.p));
+                k_optab<<<grid_for(uint64_t(count) * metas.size()), THREADS, 0, cs>>>(
+                    static_cast<const TrajOpMeta *>(d_meta.p), uint32_t(metas.size()),
+                    reinterpret_cast<const float2 *>(d_mtab.p), m, count, static_cast<const uint64_t *>(d_fb.p),
+                    static_cast<TrajRec *>(d_recs.p));
+                cudaError_t e3 = traj_plan_run(tp, reinterpret_cast<float2 *>(states), count,
+                                               static_cast<const TrajRec *>(d_recs.p), cs);
+                k_metric_frame<R><<<grid_for(count), THREADS, 0, cs>>>(
+                    states, n, count, static_cast<const uint64_t *>(d_x0.p), g.target,
+                    g.metric == QS_TRAJ_FIDELITY ? 1 : 0, static_cast<const uint64_t *>(d_fb.p), m,
+                    static_cast<double *>(d_metric.p));
+                e2 = cudaStreamEndCapture(cs, &graph);
+                if (e2 == cudaSuccess && e3 != cudaSuccess) e2 = e3;
+            }
+            if (e2 == cudaSuccess) e2 = cudaGraphInstantiate(&exec, graph, 0);
+            if (e2 == cudaSuccess) e2 = cudaGraphLaunch(exec, cs);
+            if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(cs);
+            if (exec) cudaGraphExecDestroy(exec);
+            if (graph) cudaGraphDestroy(graph);
+            if (cs) cudaStreamDestroy(cs);
+            st = ck(e2, "fused trajectories");
+        }
+        traj_plan_destroy(tp);
+        if (st != QS_OK) return st;
+        if ((st = ck(cudaMemcpy(metric, d_metric.p, sizeof(double) * count, cudaMemcpyDeviceToHost), "results")) != QS_OK)
+            return st;
+        if (stats)
+            if ((st = ck(cudaMemcpy(stats, d_stats.p, sizeof(uint64_t) * 4 * count, cudaMemcpyDeviceToHost), "results")) != QS_OK)
+                return st;
+        return QS_OK;
+    }
     const StepDesc *dsteps = static_cast<const StepDesc *>(d_steps.p);
     for (int s = 0; s < m; ++s) {
         const int free_bits = n - steps[s].nfixed;
@@ -443,7 +739,10 @@ qs_status run_group(const qs_traj_group &g, const qs_noise &nz, uint64_t seed, d
 using namespace qs;
 
 extern "C" qs_status qs_run_trajectories(const qs_traj_group *groups, int n_groups, const qs_noise *noise,
-                                         uint64_t seed, qs_dtype dt, double *metric, uint64_t *stats) {
+                                         uint64_t seed, qs_dtype dt, const qs_traj_opts *opts, double *metric,
+                                         uint64_t *stats) {
+    const int fuse_mode = opts ? (opts->no_fusion ? 0 : 1) : 1;
+    const int max_ops = opts ? opts->max_ops_per_pass : 0;
     if (!groups || n_groups < 0 || !noise || !metric) return fail(QS_EINVAL, "NULL argument");
     if (dt != QS_C64 && dt != QS_C128) return fail(QS_EINVAL, "bad dtype");
     if (!(noise->p >= 0.0 && noise->p <= 1.0) || !(noise->sigma >= 0.0) || !std::isfinite(noise->sigma))
@@ -460,8 +759,10 @@ extern "C" qs_status qs_run_trajectories(const qs_traj_group *groups, int n_grou
         for (uint32_t i = 0; i < g.count; ++i)
             if (g.x0[i] >> g.n) return fail(QS_ERANGE, "trajectory group: x0 >= 2^n");
         if (g.m > (size_t(1) << 31)) return fail(QS_ERANGE, "trajectory group: too many gates");
-        qs_status st = dt == QS_C64 ? run_group<float>(g, *noise, seed, metric + off, stats ? stats + 4 * off : nullptr)
-                                    : run_group<double>(g, *noise, seed, metric + off, stats ? stats + 4 * off : nullptr);
+        qs_status st = dt == QS_C64 ? run_group<float>(g, *noise, seed, metric + off, stats ? stats + 4 * off : nullptr,
+                                                       fuse_mode, max_ops)
+                                    : run_group<double>(g, *noise, seed, metric + off, stats ? stats + 4 * off : nullptr,
+                                                        fuse_mode, max_ops);
         if (st != QS_OK) return st;
         off += g.count;
     }

@@ -159,3 +159,32 @@ def test_paper_ht_experiment_n20(mode, p, sigma):
         want = ((1 + math.exp(-9 * sigma ** 2 * k / 4)) / 2) ** n
     se = met.std() / math.sqrt(T)
     assert abs(met.mean() - want) < 4 * se + 2e-3, (met.mean(), want, se)
+
+
+@pytest.mark.parametrize("mode", [qs.NOISE_FLIPS, qs.NOISE_DEPOLARIZING])
+@pytest.mark.parametrize("max_ops", [0, 6, 60])
+def test_fused_trajectories_match_plain_and_oracle(mode, max_ops):
+    # the fused path (Pauli frame folded into the gates) against the plain
+    # path (flips applied to the states) and the oracle's replay
+    n = 11
+    seed = 0xABCDEF
+    r = W.rng(21)
+    x0 = r.integers(0, 1 << n, size=20, dtype=np.uint64)
+    k = 333
+    groups = [{"n": n, "gates": W.noisy_synthesis(W.qft_circuit(n)), "x0": x0, "first": 0},
+              {"n": n, "gates": W.noisy_synthesis(W.grover_circuit(n, k, 6)), "x0": np.zeros(10, np.uint64),
+               "first": 20, "metric": "prob", "target": k}]
+    p, sigma = 0.01, 0.03
+    mf, sf = qs.run_trajectories(groups, p, sigma, seed, dtype="c64", mode=mode, fuse=True, max_ops=max_ops)
+    mp, sp = qs.run_trajectories(groups, p, sigma, seed, dtype="c64", mode=mode, fuse=False)
+    assert np.array_equal(sf, sp)
+    assert np.max(np.abs(mf - mp)) < 2e-5
+    assert int(sf[:, :3].sum()) > 20
+    for i in (0, 7, 19):
+        m, s = oracle_metric(n, groups[0]["gates"], p, sigma, seed, i, int(x0[i]), "fidelity", 0, mode=mode)
+        assert list(s) == [int(v) for v in sf[i]]
+        assert abs(m - mf[i]) < 2e-5
+    for i in (20, 29):
+        m, s = oracle_metric(n, groups[1]["gates"], p, sigma, seed, i, 0, "prob", k, mode=mode)
+        assert list(s) == [int(v) for v in sf[i]]
+        assert abs(m - mf[i]) < 2e-5
