@@ -93,6 +93,7 @@ def lib() -> ctypes.CDLL:
     L.or_expect_pauli.restype = ctypes.c_double
     L.or_measure.argtypes = [dp, ctypes.c_int, ctypes.c_double]
     L.or_measure.restype = ctypes.c_uint64
+    L.or_qft_dft.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     L.or_gate_matrix.argtypes = [ctypes.c_int, dp, dp, dp]
     L.or_gate_n_angles.argtypes = [ctypes.c_int]
     L.or_philox4x32_10.argtypes = [ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32),
@@ -198,6 +199,18 @@ def expect_pauli(psi: np.ndarray, pauli: str) -> float:
 def measure(psi: np.ndarray, r: float) -> int:
     n = int(np.log2(psi.size))
     return int(lib().or_measure(_dp(np.ascontiguousarray(psi).view(np.float64)), n, r))
+
+
+def qft(psi: np.ndarray, q0: int = 0, L: Optional[int] = None, inverse: bool = False) -> np.ndarray:
+    """QFT (or its inverse) of qubits q0 .. q0+L-1 by the plain double sum of
+    Sec. 2.3.2; returns a new vector."""
+    n = int(np.log2(psi.size))
+    if L is None:
+        L = n - q0
+    out = np.array(psi, dtype=np.complex128, copy=True)
+    if lib().or_qft_dft(_dp(out.view(np.float64)), n, q0, L, int(bool(inverse))) != 0:
+        raise ValueError("or_qft_dft: bad arguments")
+    return out
 
 
 def philox(ctr, key) -> np.ndarray:

@@ -344,6 +344,39 @@ uint64_t or_measure(const double *psi, int n, double r)
 }
 
 /* ------------------------------------------------------------------------- */
+/* Quantum Fourier transform as a black-box operator, Sec. 2.3.2:              */
+/*   beta_x = 2^{-L/2} sum_y w^{x y} alpha_y,  w = e^{2 pi i / 2^L}            */
+/* on the L qubits q0 .. q0+L-1 (qubit q0 the most significant of that         */
+/* register; the other qubits are spectators), written as the plain double     */
+/* sum (O(2^n 2^L), no fast transform).  inverse != 0 uses w^{-1}.  The         */
+/* exponent x*y is reduced modulo 2^L in integers before the angle is formed.  */
+/* ------------------------------------------------------------------------- */
+int or_qft_dft(double *psi, int n, int q0, int L, int inverse)
+{
+    if (n < 1 || n > 30 || q0 < 0 || L < 1 || q0 + L > n) return -1;
+    const uint64_t N = (uint64_t)1 << n, M = (uint64_t)1 << L;
+    const int lo = n - q0 - L;                 /* index bit of the least significant qubit */
+    const uint64_t field = (M - 1) << lo;
+    const double sgn = inverse ? -1.0 : 1.0, scale = 1.0 / sqrt((double)M);
+    cplx *a = (cplx *)psi;
+    cplx *out = (cplx *)calloc(N, sizeof(cplx));
+    if (!out) return -1;
+    for (uint64_t i = 0; i < N; i++) {         /* output index i = (rest, x) */
+        const uint64_t x = (i & field) >> lo, rest = i & ~field;
+        cplx s = 0.0;
+        for (uint64_t y = 0; y < M; y++) {
+            const uint64_t e = (x * y) & (M - 1);
+            const double ang = sgn * 2.0 * M_PI * (double)e / (double)M;
+            s += cexp(I * ang) * a[rest | (y << lo)];
+        }
+        out[i] = s * scale;
+    }
+    memcpy(a, out, N * sizeof(cplx));
+    free(out);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Philox4x32-10 (Salmon et al., SC'11).  Counter (c0..c3), key (k0, k1).     */
 /* One round: multiply c0 and c2 by the two round multipliers into 64-bit      */
 /* products; the new words are (hi(c2*M1) ^ c1 ^ k0, lo(c2*M1),               */

@@ -164,6 +164,68 @@ def test_qft_gate_count_n10():
     assert sum(1 for x in g if x.kind == "SWAP") == 5
 
 
+def dft_matrix(L, inverse=False):
+    """2^{-L/2} w^{xy} built from numpy's FFT of the identity columns."""
+    M = 1 << L
+    eye = np.eye(M, dtype=complex)
+    return (np.fft.fft(eye, axis=0) if inverse else np.fft.ifft(eye, axis=0) * M) / math.sqrt(M)
+
+
+@pytest.mark.parametrize("n", [1, 2, 4, 7, 10])
+def test_qft_black_box_whole_register(n):
+    # the QFT as a black box (Sec. 2.3.2) on random vectors against numpy's
+    # inverse FFT times 2^{n/2}, and against the oracle's own gate-by-gate
+    # QFT circuit; the inverse undoes it
+    r = W.rng(600 + n)
+    psi = random_state(r, n)
+    got = oracle.qft(psi)
+    assert np.linalg.norm(got - np.fft.ifft(psi) * math.sqrt(1 << n)) < 1e-12
+    assert np.linalg.norm(got - oracle.run(n, W.qft_circuit(n), psi=psi)) < 1e-12
+    back = oracle.qft(got, inverse=True)
+    assert np.linalg.norm(back - psi) < 1e-12
+    assert np.linalg.norm(oracle.qft(psi, inverse=True) - np.fft.fft(psi) / math.sqrt(1 << n)) < 1e-12
+
+
+@pytest.mark.parametrize("n,q0,L", [(3, 0, 1), (4, 1, 2), (6, 2, 3), (7, 0, 4), (7, 3, 4), (8, 5, 3)])
+def test_qft_black_box_sub_register(n, q0, L):
+    # QFT of qubits q0..q0+L-1 = I_{2^q0} (x) F_{2^L} (x) I_{2^{n-q0-L}} with
+    # qubit 0 the most significant (Kronecker order = qubit order), and the
+    # same sub-register circuit applied gate by gate
+    r = W.rng(700 + 16 * n + q0)
+    psi = random_state(r, n)
+    for inv in (False, True):
+        Umat = np.kron(np.kron(np.eye(1 << q0), dft_matrix(L, inv)), np.eye(1 << (n - q0 - L)))
+        assert np.linalg.norm(oracle.qft(psi, q0, L, inverse=inv) - Umat @ psi) < 1e-12
+    assert np.linalg.norm(oracle.qft(psi, q0, L) - oracle.run(n, W.qft_circuit(n, q0, L), psi=psi)) < 1e-12
+
+
+def test_qft_black_box_rejects_bad_ranges():
+    psi = random_state(W.rng(1), 4)
+    for q0, L in ((0, 0), (3, 2), (-1, 2)):
+        with pytest.raises(ValueError):
+            oracle.qft(psi, q0, L)
+
+
+@pytest.mark.parametrize("L,eps", [(8, 1e-2), (12, 1e-3)])
+def test_approximate_qft_error_bound(L, eps):
+    # the approximate QFT (Sec. 2.3.2) drops the phase shifts of index
+    # k > max_k; every dropped gate differs from the identity by
+    # |e^{i 2 pi / 2^k} - 1| <= 2 pi / 2^k, so the operator-norm error is at
+    # most the sum of those; checked against the exact transform on random
+    # states, and the gate count is O(L log(L / eps))
+    mk = W.approx_qft_max_k(L, eps)
+    full, approx = W.qft_circuit(L), W.qft_circuit(L, max_k=mk)
+    dropped = [g for g in full if g.kind == "UP1" and g.angles[0] < 2 * math.pi / (1 << mk) - 1e-15]
+    assert len(full) - len(approx) == len(dropped)
+    bound = sum(2 * math.pi / (1 << round(math.log2(2 * math.pi / g.angles[0]))) for g in dropped)
+    assert sum(1 for g in approx if g.kind == "UP1") <= L * mk
+    r = W.rng(800 + L)
+    for _ in range(3):
+        psi = random_state(r, L)
+        e = np.linalg.norm(oracle.run(L, approx, psi=psi) - oracle.qft(psi))
+        assert 0 < e <= bound + 1e-12
+
+
 @pytest.mark.parametrize("n", [1, 3, 6, 8])
 def test_hadamard_transform(n):
     # Sec. 2.3.1: H_n|x> = 2^{-n/2} sum_y (-1)^{x.y}|y>; scipy's Sylvester

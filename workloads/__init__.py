@@ -75,21 +75,35 @@ def hadamard_layer(n: int) -> List[Gate]:
     return [Gate("H", q) for q in range(n)]
 
 
-def qft_circuit(n: int) -> List[Gate]:
-    """The textbook QFT circuit for beta_x = 2^{-n/2} sum_y w^{xy} alpha_y with
-    w = e^{2 pi i / 2^n} (Sec. 2.3.2): for each qubit j, H on j followed by
-    the phase shifts diag(1, e^{2 pi i / 2^k}) on target j controlled by qubit
-    j+k-1, k = 2..n-j; then SWAP(j, n-1-j) reverses the qubit order.  The paper's
-    R_d = diag(1, e^{i pi / 2^d}) is the same gate with d = k - 1."""
+def qft_circuit(n: int, q0: int = 0, L: Optional[int] = None, max_k: Optional[int] = None) -> List[Gate]:
+    """The textbook QFT circuit for beta_x = 2^{-L/2} sum_y w^{xy} alpha_y with
+    w = e^{2 pi i / 2^L} (Sec. 2.3.2) on the L qubits q0 .. q0+L-1 (q0 the most
+    significant; L defaults to n - q0): for each qubit j of the register, H on j
+    followed by the phase shifts diag(1, e^{2 pi i / 2^k}) on target j controlled
+    by qubit j+k-1, k = 2..; then SWAPs reverse the register's qubit order.  The
+    paper's R_d = diag(1, e^{i pi / 2^d}) is the same gate with d = k - 1.
+
+    max_k: the approximate QFT of Sec. 2.3.2 -- phase shifts with k > max_k
+    (angles below 2 pi / 2^max_k, which act on distant qubits) are left out."""
+    if L is None:
+        L = n - q0
     gates: List[Gate] = []
-    for j in range(n):
-        gates.append(Gate("H", j))
-        for k in range(2, n - j + 1):
-            gates.append(Gate("UP1", j, controls={j + k - 1: 1},
+    for j in range(L):
+        gates.append(Gate("H", q0 + j))
+        for k in range(2, L - j + 1):
+            if max_k is not None and k > max_k:
+                break
+            gates.append(Gate("UP1", q0 + j, controls={q0 + j + k - 1: 1},
                               angles=(2.0 * math.pi / (1 << k),)))
-    for j in range(n // 2):
-        gates.append(Gate("SWAP", j, target2=n - 1 - j))
+    for j in range(L // 2):
+        gates.append(Gate("SWAP", q0 + j, target2=q0 + L - 1 - j))
     return gates
+
+
+def approx_qft_max_k(L: int, eps: float) -> int:
+    """Largest phase-shift index k kept by the approximate QFT of accuracy eps
+    (Sec. 2.3.2: O(L log(L / eps)) gates): k <= ceil(log2(L / eps)), at least 2."""
+    return max(2, int(math.ceil(math.log2(L / eps))))
 
 
 def phase_flip(n: int, index: int, phi: float = math.pi) -> Gate:
