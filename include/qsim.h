@@ -230,6 +230,20 @@ qs_status qs_renormalize(qs_state *s);
  * At most 2^26 shots per call (QS_ERANGE).  Synchronous. */
 qs_status qs_measure(qs_state *s, const double *r, size_t shots, uint64_t *out);
 
+/* Quantum Fourier transform as a black-box operator (Sec. 2.3.2: the paper
+ * replaces the QFT circuit by a classical FFT when the circuit is taken to be
+ * error free): on the L qubits q0 .. q0+L-1, qubit q0 the most significant of
+ * that register and the other qubits spectators,
+ *     beta_x = 2^{-L/2} sum_y w^{x y} alpha_y,  w = e^{2 pi i / 2^L}
+ * (inverse != 0: w = e^{-2 pi i / 2^L}, the adjoint).  With q0 = 0, L = n it
+ * equals the QFT circuit of Sec. 2.3.2 including its final qubit reversal.
+ * In place, in the state's precision (twiddles from double-precision
+ * tables).  Needs 0 <= q0, 1 <= L, q0 + L <= n, else QS_EINVAL.
+ * Asynchronous on the state's stream; allocates a small twiddle table
+ * (2^12 + 2^ceil(L/2) + 2^floor(L/2) complex entries) with the stream-ordered
+ * allocator for the duration of the call (QS_ECUDA if that fails). */
+qs_status qs_qft(qs_state *s, int q0, int L, int inverse);
+
 /* Norm of a state without any allocation, for callers that cannot allocate
  * device memory at the point they need it (a framework that owns the whole
  * device memory budget through its own pool, a latency-critical loop in which

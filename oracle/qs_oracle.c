@@ -360,17 +360,18 @@ int or_qft_dft(double *psi, int n, int q0, int L, int inverse)
     const double sgn = inverse ? -1.0 : 1.0, scale = 1.0 / sqrt((double)M);
     cplx *a = (cplx *)psi;
     cplx *out = (cplx *)calloc(N, sizeof(cplx));
-    if (!out) return -1;
-    for (uint64_t i = 0; i < N; i++) {         /* output index i = (rest, x) */
+    cplx *w = (cplx *)malloc(M * sizeof(cplx));   /* w^e, e < 2^L */
+    if (!out || !w) { free(out); free(w); return -1; }
+    for (uint64_t e = 0; e < M; e++) w[e] = cexp(I * (sgn * 2.0 * M_PI * (double)e / (double)M));
+#pragma omp parallel for schedule(static)
+    for (int64_t ii = 0; ii < (int64_t)N; ii++) {   /* output index i = (rest, x) */
+        const uint64_t i = (uint64_t)ii;
         const uint64_t x = (i & field) >> lo, rest = i & ~field;
         cplx s = 0.0;
-        for (uint64_t y = 0; y < M; y++) {
-            const uint64_t e = (x * y) & (M - 1);
-            const double ang = sgn * 2.0 * M_PI * (double)e / (double)M;
-            s += cexp(I * ang) * a[rest | (y << lo)];
-        }
+        for (uint64_t y = 0; y < M; y++) s += w[(x * y) & (M - 1)] * a[rest | (y << lo)];
         out[i] = s * scale;
     }
+    free(w);
     memcpy(a, out, N * sizeof(cplx));
     free(out);
     return 0;

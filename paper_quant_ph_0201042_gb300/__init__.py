@@ -110,6 +110,7 @@ _SIGS = {
     "qs_inner": [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(C128)],
     "qs_norm": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)],
     "qs_renormalize": [ctypes.c_void_p],
+    "qs_qft": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int],
     "qs_measure": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_size_t,
                    ctypes.POINTER(ctypes.c_uint64)],
     "qs_norm_noalloc": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p],
@@ -299,6 +300,14 @@ class State:
         check(lib().qs_measure(self._h, rr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), rr.size,
                                out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))))
         return out[:rr.size]
+
+    def qft(self, q0: int = 0, L: Optional[int] = None, inverse: bool = False) -> "State":
+        """QFT (inverse: its adjoint) of qubits q0 .. q0+L-1 by the library's
+        FFT (qs_qft); L defaults to n - q0."""
+        if L is None:
+            L = self.n - q0
+        check(lib().qs_qft(self._h, int(q0), int(L), int(bool(inverse))))
+        return self
 
     # host copies
     def to_numpy(self) -> np.ndarray:
