@@ -104,7 +104,7 @@ def lib() -> ctypes.CDLL:
     L.or_gauss.restype = ctypes.c_double
     L.or_run_trajectory.argtypes = [dp, ctypes.c_int, gp, ctypes.c_int64, ctypes.POINTER(OrNoise),
                                     ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64,
-                                    ctypes.POINTER(ctypes.c_uint64)]
+                                    ctypes.POINTER(ctypes.c_uint64), ctypes.c_void_p]
     L.or_cost.argtypes = [ctypes.c_int, gp, ctypes.c_int64, dp, ctypes.c_char_p, dp]
     L.or_cost.restype = ctypes.c_double
     L.or_gradient.argtypes = [ctypes.c_int, gp, ctypes.c_int64, dp, ctypes.c_int64, ctypes.c_char_p,
@@ -229,16 +229,25 @@ def gauss(seed: int, traj: int, step: int, a: int) -> float:
     return lib().or_gauss(seed, traj, step, a)
 
 
+NO_DEVIATION = 1   # gate flag: its angles are not deviated
+NO_FLIPS = 2       # gate flag: no flips after it
+
+
 def run_trajectory(n: int, gates: Sequence, p: float, sigma: float, seed: int, traj: int,
-                   x0: int, mode: int = NOISE_FLIPS, every: int = 1):
+                   x0: int, mode: int = NOISE_FLIPS, every: int = 1, flags=None):
     """One noisy trajectory (Sec. 3 error model); returns (state, stats) with
     stats = [#X flips, #Y flips, #Z flips, event fingerprint].  Decoherence acts after
-    gate step s when (s + 1) % every == 0."""
+    gate step s when (s + 1) % every == 0 and flags[s] lacks NO_FLIPS."""
     psi = np.zeros(1 << n, dtype=np.complex128)
     nz = OrNoise(p, sigma, mode, every)
     st = (ctypes.c_uint64 * 4)()
+    fl = None
+    if flags is not None:
+        fl = np.ascontiguousarray(flags, dtype=np.uint8)
+        assert fl.size == len(gates)
     rc = lib().or_run_trajectory(_dp(psi.view(np.float64)), n, gates_to_c(gates), len(gates),
-                                 ctypes.byref(nz), seed, traj, x0, st)
+                                 ctypes.byref(nz), seed, traj, x0, st,
+                                 fl.ctypes.data_as(ctypes.c_void_p) if fl is not None else None)
     if rc != 0:
         raise ValueError("oracle: invalid gate in trajectory circuit")
     return psi, np.array(list(st), dtype=np.uint64)

@@ -465,9 +465,13 @@ static uint64_t mix64(uint64_t z)
  * stats[1] = Y flips, stats[2] = Z flips, stats[3] = fingerprint of the flip
  * events: the sum (mod 2^64) of mix64((s * 64 + q) * 4 + kind) over events
  * (kind 1 = X, 2 = Y, 3 = Z), which does not depend on their order. */
+/* flags (may be NULL): per gate, bit 0 = its angles are not deviated, bit 1 =
+ * no flips are drawn after it (a noiseless preparation; decoherence only
+ * after chosen gates, as the phase shifts R_d of the QFT experiment of
+ * Sec. 5.2).  The draws of the other gates keep their counters. */
 int or_run_trajectory(double *psi_out, int n, const or_gate *g, int64_t m,
                       const or_noise *noise, uint64_t seed, uint32_t traj,
-                      uint64_t x0, uint64_t *stats)
+                      uint64_t x0, uint64_t *stats, const uint8_t *flags)
 {
     cplx *psi = (cplx *)psi_out;
     or_init_basis(psi_out, n, x0);
@@ -478,12 +482,13 @@ int or_run_trajectory(double *psi_out, int n, const or_gate *g, int64_t m,
         /* the gate, with its angles deviated (Sec. 3.2) */
         double ang[2] = { g[s].angle[0], g[s].angle[1] };
         int na = or_gate_n_angles(g[s].kind);
-        if (noise->sigma != 0.0)
+        const int fl = flags ? flags[s] : 0;
+        if (noise->sigma != 0.0 && !(fl & 1))
             for (int a = 0; a < na; a++)
                 ang[a] += noise->sigma * or_gauss(seed, traj, (uint32_t)s, (uint32_t)a);
         if (apply_gate_angles(psi, n, &g[s], ang) != 0) return -1;
         /* then decoherence on every qubit (Sec. 3.1) */
-        if (T == 0) continue;
+        if (T == 0 || (fl & 2)) continue;
         if (noise->every > 1 && (s + 1) % noise->every != 0) continue;
         for (int q = 0; q < n; q++) {
             uint32_t ctr[4] = { traj, (uint32_t)s, (uint32_t)q, 0u };

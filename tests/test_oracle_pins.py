@@ -437,6 +437,25 @@ def test_operational_closed_form_matches_quadrature():
             assert abs(rho[0, 0].real - (1 + math.exp(-9 * sigma ** 2 * k / 4)) / 2) < 1e-12
 
 
+def test_trajectory_gate_flags():
+    # per-gate flags: flips only after the last gate of each Hadamard layer is
+    # the same draw sequence as every = n (bit for bit); no deviation on any
+    # gate is the sigma = 0 trajectory; a noiseless preparation leaves the
+    # prepared state exact
+    n, k = 4, 6
+    gates = W.noisy_synthesis(W.hadamard_layer(n) * k)
+    fl = [0 if (s + 1) % n == 0 else oracle.NO_FLIPS for s in range(len(gates))]
+    for t in range(20):
+        a = oracle.run_trajectory(n, gates, 0.05, 0.02, 7, t, 0, mode=oracle.NOISE_DEPOLARIZING, every=n)
+        b = oracle.run_trajectory(n, gates, 0.05, 0.02, 7, t, 0, mode=oracle.NOISE_DEPOLARIZING, flags=fl)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+        c = oracle.run_trajectory(n, gates, 0.0, 0.3, 7, t, 0, flags=[oracle.NO_DEVIATION] * len(gates))
+        assert np.linalg.norm(c[0] - oracle.run(n, gates)) < 1e-13
+    prep = W.noisy_synthesis(W.hadamard_layer(n))
+    d = oracle.run_trajectory(n, prep, 0.5, 0.3, 7, 0, 0, flags=[3] * n)
+    assert np.allclose(d[0], np.full(1 << n, 2 ** (-n / 2))) and list(d[1]) == [0, 0, 0, 0]
+
+
 def test_trajectory_draws_are_deterministic():
     n = 4
     gates = W.noisy_synthesis(W.qft_circuit(n))
