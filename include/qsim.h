@@ -312,7 +312,15 @@ enum { QS_TRAJ_FIDELITY = 0, QS_TRAJ_PROB = 1 };
  *           (the amplitude of the marked element, Sec. 5.3)
  *   first   id of the group's first trajectory; trajectory first + i draws
  *           from the Philox4x32-10 stream with counter word 0 = first + i
- *   x0      initial basis index of each of the `count` trajectories */
+ *   x0      initial basis index of each of the `count` trajectories
+ *   flags   NULL, or one byte per gate: QS_TRAJ_NO_DEVIATION (its angles are
+ *           not deviated), QS_TRAJ_NO_FLIPS (no flips are drawn after it).
+ *           A noiseless state preparation is a prefix of gates with both
+ *           flags; the QFT experiment of Sec. 5.2 (decoherence after each
+ *           phase shift R_d only) sets QS_TRAJ_NO_FLIPS on the other gates.
+ *           Flags change no counter: the draws of the other gates are the
+ *           same as without them. */
+enum { QS_TRAJ_NO_DEVIATION = 1, QS_TRAJ_NO_FLIPS = 2 };
 typedef struct {
     int32_t n;
     int32_t metric;
@@ -322,6 +330,7 @@ typedef struct {
     uint32_t first;
     uint32_t count;
     const uint64_t *x0;
+    const uint8_t *flags;
 } qs_traj_group;
 
 /* Runs every trajectory of every group on the current device and writes the

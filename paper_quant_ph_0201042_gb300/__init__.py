@@ -60,7 +60,8 @@ class QsNoise(ctypes.Structure):
 class QsTrajGroup(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("metric", ctypes.c_int32), ("target", ctypes.c_uint64),
                 ("gates", ctypes.POINTER(QsGate)), ("m", ctypes.c_size_t), ("first", ctypes.c_uint32),
-                ("count", ctypes.c_uint32), ("x0", ctypes.POINTER(ctypes.c_uint64))]
+                ("count", ctypes.c_uint32), ("x0", ctypes.POINTER(ctypes.c_uint64)),
+                ("flags", ctypes.c_void_p)]
 
 
 class QsObservable(ctypes.Structure):
@@ -72,6 +73,8 @@ OBS_PAULI = 0
 OBS_FIDELITY = 1
 NOISE_FLIPS = 0
 NOISE_DEPOLARIZING = 1
+TRAJ_NO_DEVIATION = 1
+TRAJ_NO_FLIPS = 2
 TRAJ_FIDELITY = 0
 TRAJ_PROB = 1
 
@@ -379,9 +382,10 @@ def run_trajectories(groups: Sequence, p: float, sigma: float, seed: int, dtype:
     """Runs batches of noisy trajectories (qs_run_trajectories).
 
     groups: sequence of dicts with keys n, gates, x0 (array of basis indices),
-    first (trajectory id of the first), metric ('fidelity' or 'prob') and
-    target (for 'prob').  Returns (metric array, stats array of shape (T, 4)
-    or None) in group order."""
+    first (trajectory id of the first), metric ('fidelity' or 'prob'),
+    target (for 'prob') and optionally flags (one byte per gate:
+    TRAJ_NO_DEVIATION | TRAJ_NO_FLIPS).  Returns (metric array, stats array of
+    shape (T, 4) or None) in group order."""
     keep = []
     arr = (QsTrajGroup * max(1, len(groups)))()
     total = 0
@@ -398,6 +402,12 @@ def run_trajectories(groups: Sequence, p: float, sigma: float, seed: int, dtype:
         c.first = int(g["first"])
         c.count = int(x0.size)
         c.x0 = x0.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+        if g.get("flags") is not None:
+            fl = np.ascontiguousarray(g["flags"], dtype=np.uint8)
+            if fl.size != len(g["gates"]):
+                raise ValueError("flags: one byte per gate")
+            keep.append(fl)
+            c.flags = fl.ctypes.data_as(ctypes.c_void_p)
         total += x0.size
     nz = QsNoise(p, sigma, mode, every)
     met = np.zeros(max(1, total), dtype=np.float64)

@@ -102,7 +102,7 @@ struct StepDesc {          // one gate step of a group, as the kernels see it
     int32_t cls;           // TrajClass
     int32_t bit, bit2;     // target (and second SWAP) index bits
     int32_t nang;          // angles deviated by operational errors
-    int32_t pad;
+    int32_t flags;         // QS_TRAJ_NO_DEVIATION | QS_TRAJ_NO_FLIPS
     uint64_t cmask, cval;  // controls (index bits)
     double theta[2];
     double u[8];           // ideal matrix (MATRIX gates, echo steps)
@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(THREADS) k_noise(const StepDesc *__restrict__ 
         const uint32_t traj = first + b;
         const StepDesc &d = steps[s];
         double ang[2] = {d.theta[0], d.theta[1]};
-        if (sigma != 0.0)
+        if (sigma != 0.0 && !(d.flags & QS_TRAJ_NO_DEVIATION))
             for (int a = 0; a < d.nang; ++a) ang[a] += sigma * gauss(traj, s, uint32_t(a), k0, k1);
         double u[8];
         synth(d.kind, ang[0], ang[1], d.u, u);
@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(THREADS) k_noise(const StepDesc *__restrict__ 
         for (int k = 0; k < 4; ++k) mt[k] = mk<R>(R(u[2 * k]), R(u[2 * k + 1]));
         uint64_t xm = 0, zm = 0;
         int ny = 0;
-        if (thr != 0 && (every <= 1 || (s + 1) % uint32_t(every) == 0)) {
+        if (thr != 0 && !(d.flags & QS_TRAJ_NO_FLIPS) && (every <= 1 || (s + 1) % uint32_t(every) == 0)) {
             for (int q = 0; q < n; ++q) {
                 const uint4 w = philox(make_uint4(traj, s, uint32_t(q), 0u), k0, k1);
                 if (w.x >= thr) continue;
@@ -590,7 +590,10 @@ qs_status run_group(const qs_traj_group &g, const qs_noise &nz, uint64_t seed, d
         if (st != QS_OK) return st;
     }
     std::vector<StepDesc> steps;
-    for (const HostOp &o : ops) steps.push_back(make_step(o));
+    for (size_t k = 0; k < ops.size(); ++k) {
+        steps.push_back(make_step(ops[k]));
+        steps.back().flags = g.flags ? int32_t(g.flags[k] & 3u) : 0;
+    }
     std::vector<StepDesc> echo;
     if (g.metric == QS_TRAJ_FIDELITY)
         for (size_t k = ops.size(); k-- > 0;) echo.push_back(inverse_step(ops[k]));

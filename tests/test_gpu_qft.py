@@ -100,3 +100,25 @@ def test_qft_n30_full_size(dtype):
     s.qft(inverse=True)
     assert abs(s.prob(x) - 1) < (1e-12 if dtype == "c128" else 1e-5)
     assert abs(s.norm() - 1) < (1e-12 if dtype == "c128" else 1e-5)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("n,eps", [(12, 1e-2), (16, 1e-3)])
+def test_approximate_qft_circuit(dtype, n, eps):
+    # the approximate QFT of Sec. 2.3.2 (phase shifts with k > ceil(log2(n /
+    # eps)) left out) through the fused planner, against the oracle's gate by
+    # gate run of the same circuit, and within the dropped gates' bound of the
+    # exact transform (the black box)
+    mk = W.approx_qft_max_k(n, eps)
+    approx = W.qft_circuit(n, max_k=mk)
+    assert len(approx) < len(W.qft_circuit(n))
+    psi = random_state(W.rng(4200 + n), n)
+    if dtype == "c64":
+        psi = psi.astype(np.complex64).astype(np.complex128)
+    want = oracle.run(n, approx, psi=psi)
+    got = qs.State(n, dtype).from_numpy(psi).apply_circuit(approx).to_numpy().astype(np.complex128)
+    assert np.linalg.norm(got - want) < (1e-12 if dtype == "c128" else 1e-5)
+    exact = qs.State(n, dtype).from_numpy(psi).qft().to_numpy().astype(np.complex128)
+    dropped = sum(1 for j in range(n) for k in range(mk + 1, n - j + 1))
+    bound = sum(2 * math.pi / (1 << k) for j in range(n) for k in range(mk + 1, n - j + 1))
+    assert dropped > 0 and np.linalg.norm(got - exact) <= bound + 1e-5

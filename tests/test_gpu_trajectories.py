@@ -188,3 +188,30 @@ def test_fused_trajectories_match_plain_and_oracle(mode, max_ops):
         m, s = oracle_metric(n, groups[1]["gates"], p, sigma, seed, i, 0, "prob", k, mode=mode)
         assert list(s) == [int(v) for v in sf[i]]
         assert abs(m - mf[i]) < 2e-5
+
+
+@pytest.mark.parametrize("n", [8, 11])
+@pytest.mark.parametrize("fuse", [True, False])
+def test_gate_flags_period_finding_qft(n, fuse):
+    # the QFT experiment of Sec. 5.2 at a size the oracle replays: noiseless
+    # preparation of a periodic register, deviated angles on every QFT gate,
+    # flips after the phase shifts R_d only; flags change no counter, so the
+    # flip events match the oracle bit for bit
+    gates, flags = W.period_finding_qft(n, 3, 5)
+    assert len(flags) == len(gates)
+    x0 = np.zeros(12, np.uint64)
+    p, sigma, seed = 0.01, 0.02, 0xF1A65
+    mode = qs.NOISE_DEPOLARIZING
+    groups = [{"n": n, "gates": gates, "x0": x0, "first": 40, "flags": flags}]
+    met, st = qs.run_trajectories(groups, p, sigma, seed, dtype="c64", mode=mode, fuse=fuse)
+    flips = 0
+    for i in range(12):
+        psi, s = oracle.run_trajectory(n, gates, p, sigma, seed, 40 + i, 0, mode=mode, flags=flags)
+        ideal = oracle.run(n, gates)
+        assert list(s) == [int(v) for v in st[i]], i
+        assert abs(abs(oracle.inner(ideal, psi)) ** 2 - met[i]) < 2e-5, i
+        flips += int(s[0] + s[1] + s[2])
+    assert flips > 5
+    # a noiseless run with the flags is the exact periodic-state QFT: 2^r peaks
+    m0, s0 = qs.run_trajectories(groups, 0.0, 0.0, seed, dtype="c64", fuse=fuse)
+    assert np.all(s0 == 0) and np.max(np.abs(m0 - 1)) < 1e-5

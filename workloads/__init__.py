@@ -198,6 +198,32 @@ def noisy_synthesis(gates: Sequence[Gate]) -> List[Gate]:
     return out
 
 
+NO_DEVIATION = 1   # trajectory gate flag: angles not deviated
+NO_FLIPS = 2       # trajectory gate flag: no flips after the gate
+
+
+def period_finding_qft(n: int, r_log2: int, offset: int, approx_max_k: Optional[int] = None
+                       ) -> Tuple[List[Gate], List[int]]:
+    """The QFT step of Shor's algorithm (Sec. 5.1, step 3(d); Sec. 5.2): the
+    register holds the periodic superposition sum_j |offset + j 2^r_log2>
+    (the first register after the second one was measured, the period a power
+    of two), prepared without error, then the QFT circuit in the paper's
+    synthesis.  Returns (gates, flags): the preparation (X on the offset bits,
+    H on the top n - r_log2 qubits) has no deviation and no flips; in the QFT,
+    every angle is deviated and flips follow the controlled phase shifts R_d
+    only (Sec. 5.2: decoherence each time R_d is applied)."""
+    prep: List[Gate] = []
+    for b in range(r_log2):
+        if (offset >> b) & 1:
+            prep.append(Gate("X", n - 1 - b))
+    prep += [Gate("H", q) for q in range(n - r_log2)]
+    qft = noisy_synthesis(qft_circuit(n, max_k=approx_max_k))
+    flags = [NO_DEVIATION | NO_FLIPS] * len(prep)
+    for g in qft:
+        flags.append(0 if (g.kind == "UP1" and g.controls) else NO_FLIPS)
+    return prep + qft, flags
+
+
 def basis_index(seed: int, n: int) -> int:
     """A basis state index uniform in [0, 2^n)."""
     return int(rng(seed).integers(0, 1 << n))
