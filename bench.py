@@ -284,29 +284,18 @@ def secondary(args, torch, qs, state64):
     return out
 
 
-# The paper's timing tables (Sec. 4.2, 4.3): Hadamard transform and QFT
-# circuit, complex128 (double precision as in the paper), n = 20..29.
-PAPER_HT_8PROC_S = {20: 0.40, 22: 1.35, 24: 9.58, 26: 38.71, 28: 167.31, 29: 395.81}
-PAPER_QFT_8PROC_S = {20: 5.33, 22: 23.40, 24: 137.7, 26: 526.82, 28: 2338.19, 29: 5811.49}
-
-
 def paper_tables(torch, qs):
-    """Times the paper's two circuits on this GPU (fused plans, complex128),
-    beside the paper's 8-processor Enterprise 4500 seconds."""
-    rows = []
-    for n in (20, 22, 24, 26, 28, 29):
-        st = qs.State(n, "c128")
-        for name, gates, paper in (("HT", W.hadamard_layer(n), PAPER_HT_8PROC_S[n]),
-                                   ("QFT circuit", W.qft_circuit(n), PAPER_QFT_8PROC_S[n])):
-            p = qs.Plan(n, "c128", gates)
-            step = lambda: (st.init_basis(0), p.execute(st))
-            step()
-            ms = _time(torch, step, reps=3)
-            rows.append({"circuit": name, "n": n, "gates": len(gates), "passes": p.launches, "gpu_s": ms / 1e3,
-                         "paper_8proc_s": paper, "ratio": paper / (ms / 1e3)})
-        st.close()
-        torch.cuda.empty_cache()
-    return rows
+    """The paper's tables and figures (Sec. 4.2, 4.3, 5.2) on this GPU:
+    timings of the HT, the QFT circuit and the FFT black box, and the Monte
+    Carlo error experiments (Table hod, Figs. 20d/20o, Table qft16od)."""
+    from paper_quant_ph_0201042_gb300 import paper
+    out = {"table_qft": paper.table_qft(), "table_qft_c64": paper.table_qft(dtype="c64"),
+           "table_ht": paper.table_ht()}
+    torch.cuda.empty_cache()
+    out["table_qft16od"] = paper.table_qft16()
+    out["table_hod"] = paper.table_hod()
+    out["fig20"] = paper.fig20()
+    return out
 
 
 def main():
@@ -323,7 +312,8 @@ def main():
                     help="skip the complex128, adjoint and trajectory measurements")
     ap.add_argument("--ref-budget", type=float, default=15.0)
     ap.add_argument("--paper-tables", action="store_true",
-                    help="time the paper's HT and QFT-circuit tables (n = 20..29, complex128) and exit")
+                    help="run the paper's tables (QFT circuit vs FFT, HT, Table hod, Figs. 20d/20o, "
+                         "Table qft16od) and exit")
     ap.add_argument("--qubits", "--n", dest="n", type=int, default=N_QUBITS,
                     help="qubits (profiling of smaller cases; the workload is n=30)")
     args = ap.parse_args()
