@@ -423,6 +423,27 @@ __device__ __forceinline__ bool lpred(int j, uint32_t xm, int rm, int rv) {
     return ((uint32_t(j) ^ xm) & uint32_t(rm)) == uint32_t(rv);
 }
 
+// (x, y) <- (u00 x + u01 y, u10 x + u11 y) in place.  The four output chains
+// run in lockstep and each ends on the input it replaces (x.re, x.im, y.re,
+// y.im last read by the chain that overwrites it), so the results land in
+// the registers of the inputs: no register moves where the op dispatch
+// branches join again.
+__device__ __forceinline__ void pair_inplace(float2 &x, float2 &y, const Mat4<float> &m) {
+    float A = m.u01.x * y.y, B = -m.u01.y * y.y, C = m.u10.x * x.y, D = -m.u10.y * x.y;
+    A = fmaf(m.u01.y, y.x, A);    // nx.im: u01.re y.im + u01.im y.re
+    B = fmaf(m.u01.x, y.x, B);    // nx.re: u01.re y.re - u01.im y.im
+    C = fmaf(m.u10.y, x.x, C);    // ny.im: u10.re x.im + u10.im x.re
+    D = fmaf(m.u10.x, x.x, D);    // ny.re: u10.re x.re - u10.im x.im
+    B = fmaf(-m.u00.y, x.y, B);
+    A = fmaf(m.u00.y, x.x, A);
+    D = fmaf(-m.u11.y, y.y, D);
+    C = fmaf(m.u11.y, y.x, C);
+    x.x = fmaf(m.u00.x, x.x, B);
+    x.y = fmaf(m.u00.x, x.y, A);
+    y.x = fmaf(m.u11.x, y.x, D);
+    y.y = fmaf(m.u11.x, y.y, C);
+}
+
 template <int T, bool PRED, int NA>
 __device__ __forceinline__ void s_gen(float2 (&v)[NA], Mat4<float> m, uint32_t xm, int rm, int rv) {
     if ((xm >> T) & 1) {
@@ -433,15 +454,14 @@ __device__ __forceinline__ void s_gen(float2 (&v)[NA], Mat4<float> m, uint32_t x
     for (int j = 0; j < NA; ++j) {
         if ((j >> T) & 1) continue;
         const int j1 = j | (1 << T);
-        const float2 x = v[j], y = v[j1];
-        const float2 nx = cmad2<float>(m.u00, x, m.u01, y), ny = cmad2<float>(m.u10, x, m.u11, y);
         if (PRED) {
+            const float2 x = v[j], y = v[j1];
+            const float2 nx = cmad2<float>(m.u00, x, m.u01, y), ny = cmad2<float>(m.u10, x, m.u11, y);
             const bool p = lpred(j, xm, rm, rv);
             v[j] = p ? nx : x;
             v[j1] = p ? ny : y;
         } else {
-            v[j] = nx;
-            v[j1] = ny;
+            pair_inplace(v[j], v[j1], m);
         }
     }
 }
