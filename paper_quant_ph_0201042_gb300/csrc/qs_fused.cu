@@ -1327,23 +1327,24 @@ void describe_passes(const std::vector<PassDesc<R>> &passes, const std::vector<s
                      std::string &out) {
     for (size_t k = 0; k < passes.size(); ++k) {
         const PassDesc<R> &D = passes[k];
-        int cnt[4] = {0, 0, 0, 0}, gen = 0, x = 0, hb = 0, pred = 0;
+        // register ops: general (uncontrolled / register-controlled), Hadamard
+        // butterflies, X deferred into the index mask / X moving data; lane ops
+        int rg = 0, rgc = 0, rhb = 0, rxd = 0, rx = 0, lg = 0, lx = 0, diag = 0, xp = 0;
         for (const FOp<R> &f : tables[k]) {
-            cnt[f.type]++;
-            if (f.type == OP_REG || f.type == OP_LANE) {
-                if (f.cls == GC_X) ++x;
-                else if (f.cls == GC_HB) ++hb;
-                else ++gen;
-                if (f.rmask) ++pred;
-            }
+            if (f.type == OP_XPOSE) ++xp;
+            else if (f.type == OP_DIAG) ++diag;
+            else if (f.type == OP_LANE) (f.cls == GC_X ? lx : lg)++;
+            else if (f.cls == GC_X) ((f.rmask == 0 && (f.tmask & 31u) == 0) ? rxd : rx)++;
+            else if (f.cls == GC_HB) ++rhb;
+            else (f.rmask ? rgc : rg)++;
         }
-        char line[256];
+        char line[320];
         std::string bits;
         for (int i = 0; i < D.K; ++i) bits += (i ? "," : "") + std::to_string(int(D.tile_pos[i]));
         std::snprintf(line, sizeof(line),
-                      "pass %zu: K=%d WB=%d reg=%d lane=%d diag=%d xpose=%d (gen=%d x=%d hb=%d reg-controlled=%d) bits=[%s]\n",
-                      k, D.K, D.WB, cnt[OP_REG], cnt[OP_LANE], cnt[OP_DIAG], cnt[OP_XPOSE], gen, x, hb, pred,
-                      bits.c_str());
+                      "pass %zu: K=%d WB=%d reg(gen=%d gen_ctl=%d hb=%d x_deferred=%d x_moved=%d) "
+                      "lane(gen=%d x=%d) diag=%d xpose=%d bits=[%s]\n",
+                      k, D.K, D.WB, rg, rgc, rhb, rxd, rx, lg, lx, diag, xp, bits.c_str());
         out += line;
     }
 }
