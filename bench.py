@@ -58,7 +58,9 @@ def workload_config(args, n_ranks):
         "n_qubits": n, "layers": LAYERS, "gates": LAYERS * (n + n // 2),
         "state_bytes": (8 if args.dtype == "c64" else 16) << n,
         "fused": not args.no_fuse,
-        "l2": "state (>= 8 GiB) larger than L2 (129 MB); no flush needed",
+        "l2": ("state (%d MiB) larger than L2 (129 MB); no flush needed" % (((8 if args.dtype == "c64" else 16) << n) >> 20)
+               if ((8 if args.dtype == "c64" else 16) << n) > (129 << 20) else
+               "state (%d MiB) fits L2 (129 MB): a profiling size, not the workload" % (((8 if args.dtype == "c64" else 16) << n) >> 20)),
         "parallelism": "replicas%d" % n_ranks,
     }
 
@@ -220,6 +222,15 @@ def secondary(args, torch, qs, state64):
     n = args.n
     gates = W.random_circuit(n, LAYERS, seed=SEED)
     upd = amp_updates(n, gates)
+    # the QFT black box (FFT, Sec. 2.3.2) on the same complex64 register:
+    # 4 transform passes and a bit-reversal pass, each one read + one write
+    if state64 is not None:
+        state64.qft()
+        t = _time(torch, lambda: state64.qft(), reps=3)
+        nbytes = 5 * 2 * (8 << n)
+        out["qft_fft_c64"] = {"workload": "QFT of all %d qubits by the FFT (qs_qft), complex64" % n,
+                              "ms": t, "hbm_gbs_5_passes": nbytes / (t / 1e3) / 1e9,
+                              "frac_of_measured_hbm": nbytes / (t / 1e3) / 1e9 / measured_peaks()[0]}
     # complex128: one warm-up, one timed step (FP64-ALU bound)
     if state64 is not None:
         state64.close()
