@@ -806,6 +806,64 @@ uint32_t pack_layout(const std::vector<int> &regs, const std::vector<int> &warps
     return lay;
 }
 
+// Reorders the ops of a pass within their commutation freedom so that ops
+// whose target is already a register slot run before a transpose is needed.
+// Two ops commute when every index bit they share is one on which both act
+// diagonally (a control bit, or the target of a diagonal gate): both are then
+// block diagonal over the shared bits and act on disjoint bits otherwise.
+// List scheduling: the lowest ready op (all non-commuting predecessors done)
+// that needs no transpose runs next; when there is none, the register set
+// becomes the slots the ready ops need (then the rest in order).
+std::vector<HostOp> schedule_pass(const std::vector<HostOp> &ops, const std::map<int, int> &hidx, int RB, int H) {
+    const size_t m = ops.size();
+    std::vector<uint64_t> sup(m), dg(m);
+    std::vector<int> need(m, -1);
+    for (size_t k = 0; k < m; ++k) {
+        const HostOp &o = ops[k];
+        sup[k] = support(o);
+        dg[k] = o.cmask | (is_diag(o.cls) ? uint64_t(1) << o.bit : 0);
+        if (!is_diag(o.cls) && o.bit >= LB) need[k] = hidx.at(o.bit);
+    }
+    std::vector<std::vector<int>> succ(m);
+    std::vector<int> npred(m, 0);
+    for (size_t b = 0; b < m; ++b)
+        for (size_t a = 0; a < b; ++a)
+            if ((sup[a] & sup[b]) & ~(dg[a] & dg[b])) { succ[a].push_back(int(b)); ++npred[b]; }
+    std::set<int> ready;
+    for (size_t k = 0; k < m; ++k)
+        if (npred[k] == 0) ready.insert(int(k));
+    std::vector<char> done(m, 0);
+    auto fill = [&](std::vector<int> regs) {
+        for (int k : ready)
+            if (int(regs.size()) < RB && need[k] >= 0 && std::find(regs.begin(), regs.end(), need[k]) == regs.end())
+                regs.push_back(need[k]);
+        for (size_t k = 0; k < m && int(regs.size()) < RB; ++k)
+            if (!done[k] && need[k] >= 0 && std::find(regs.begin(), regs.end(), need[k]) == regs.end())
+                regs.push_back(need[k]);
+        for (int i = 0; i < H && int(regs.size()) < RB; ++i)
+            if (std::find(regs.begin(), regs.end(), i) == regs.end()) regs.push_back(i);
+        return regs;
+    };
+    std::vector<int> regs = fill({});
+    std::vector<HostOp> out;
+    out.reserve(m);
+    while (out.size() < m) {
+        int pick = -1;
+        for (int k : ready)
+            if (need[k] < 0 || std::find(regs.begin(), regs.end(), need[k]) != regs.end()) { pick = k; break; }
+        if (pick < 0) {
+            regs = fill({});
+            pick = *ready.begin();
+        }
+        out.push_back(ops[size_t(pick)]);
+        done[size_t(pick)] = 1;
+        ready.erase(pick);
+        for (int sidx : succ[size_t(pick)])
+            if (--npred[size_t(sidx)] == 0) ready.insert(sidx);
+    }
+    return out;
+}
+
 template <typename R>
 qs_status resolve_pass(int n, int RB, int WB, const PlannedPass &pp, PassDesc<R> &D,
                        std::vector<FOp<R>> &ops_out, std::vector<TrajOpMeta> *metas = nullptr) {
@@ -820,12 +878,16 @@ qs_status resolve_pass(int n, int RB, int WB, const PlannedPass &pp, PassDesc<R>
     }
     std::map<int, int> hidx;   // global bit -> high index
     for (int i = 0; i < H; ++i) hidx[pp.high[i]] = i;
+    // state-vector plans run the pass's ops in a transpose-saving order; the
+    // trajectory mode keeps program order (its per-step Pauli frames follow it)
+    const std::vector<HostOp> sched = metas ? pp.ops : schedule_pass(pp.ops, hidx, RB, H);
+    const std::vector<HostOp> &ops = sched;
 
     // register-slot demand sequence: high index needed as a register bit by op k
-    const size_t m = pp.ops.size();
+    const size_t m = ops.size();
     std::vector<int> need(m, -1);
     for (size_t k = 0; k < m; ++k) {
-        const HostOp &o = pp.ops[k];
+        const HostOp &o = ops[k];
         if (!is_diag(o.cls) && o.bit >= LB) need[k] = hidx.at(o.bit);
     }
     // choose the register set at position k: the RB distinct bits needed
@@ -864,7 +926,7 @@ qs_status resolve_pass(int n, int RB, int WB, const PlannedPass &pp, PassDesc<R>
         return true;
     };
     for (size_t k = 0; k < m; ++k) {
-        const HostOp &o = pp.ops[k];
+        const HostOp &o = ops[k];
         if (need[k] >= 0 && std::find(regs.begin(), regs.end(), need[k]) == regs.end()) {
             // transpose: keep the slots still in demand soonest, in place
             std::vector<int> want = choose(k, {});
