@@ -272,7 +272,7 @@ def gradient(n: int, gates: Sequence, params: np.ndarray, pauli: Optional[str] =
                            pauli.encode() if pauli else None, refp,
                            0 if method == "shift" else 1, h, _dp(grad))
     if rc != 0:
-        raise ValueError("oracle: parameter used by gates of different shift classes")
+        raise ValueError("oracle: a gate parameter index beyond the parameter vector")
     return grad
 
 

@@ -566,46 +566,79 @@ static double shift_r(int kind, int which)
     }
 }
 
-/* grad[k] for k < n_params.  method 0: parameter shift
- *     dE/da = r [E(a + pi/(4r)) - E(a - pi/(4r))],
- * method 1: central finite differences [E(a + h) - E(a - h)] / (2h).
- * Each parameter must be used by gates of a single shift class; returns -1
- * otherwise. */
+/* Frequencies of E as a function of one gate's angle a.  With generator
+ * eigenvalues {-r, r} (uncontrolled rotation, or a phase shift, whose
+ * eigenvalues {0, 2r} differ by 2r) E has the single frequency 2r; a
+ * controlled rotation (RY, RZ, U_R, the U_R angle of URP1) has the generator
+ * eigenvalues {-r, 0, r} and E the frequencies r and 2r. */
+static int three_eigenvalues(const or_gate *g, int which)
+{
+    if (g->ctrl_mask == 0) return 0;
+    switch (g->kind) {
+    case OR_RY: case OR_RZ: case OR_UR: return 1;
+    case OR_URP1: return which == 0;
+    default: return 0;
+    }
+}
+
+/* grad[k] for k < n_params: the sum over the gate occurrences that use
+ * parameter k of the derivative with respect to that occurrence's angle
+ * alone (its angle is moved, the other occurrences keep theirs).
+ * method 0, parameter shift with s = r a, D(t) = E(a + t/r) - E(a - t/r):
+ *     single frequency 2r:   dE/da = r D(pi/4)
+ *     frequencies r and 2r:  dE/da = r [(1/2 - sqrt(2)/2) D(pi/2) + D(pi/4)]
+ *     (the second is exact for both: matching the sin-coefficients of
+ *      the two frequencies gives the two weights);
+ * method 1, central finite differences [E(a + h) - E(a - h)] / (2h).
+ * Returns -1 for a parameter index beyond n_params. */
+/* E with angle `which` of gate k moved to base[which] + t (the gate is given
+ * explicit angles, so other gates on the same parameter keep theirs). */
+static double eval_moved(int n, or_gate *gg, int64_t k, int64_t m, const double *params, const double base[2],
+                         int which, double t, const char *pauli, const double *ref, double *work)
+{
+    gg[k].param = -1;
+    gg[k].angle[0] = base[0] + (which == 0 ? t : 0.0);
+    gg[k].angle[1] = base[1] + (which == 1 ? t : 0.0);
+    return cost_eval(n, gg, m, params, pauli, ref, work);
+}
+
 int or_gradient(int n, const or_gate *g, int64_t m, const double *params, int64_t n_params,
                 const char *pauli, const double *ref, int method, double h, double *grad)
 {
     const uint64_t N = (uint64_t)1 << n;
-    double *p = (double *)malloc((size_t)n_params * sizeof(double));
-    double *r = (double *)calloc((size_t)n_params, sizeof(double));
+    or_gate *gg = (or_gate *)malloc((size_t)(m > 0 ? m : 1) * sizeof(or_gate));
     double *work = (double *)malloc(N * 2 * sizeof(double));
     int bad = 0;
-    memcpy(p, params, (size_t)n_params * sizeof(double));
-    for (int64_t k = 0; k < m; k++) {
+    memcpy(gg, g, (size_t)m * sizeof(or_gate));
+    for (int64_t k = 0; k < n_params; k++) grad[k] = 0.0;
+    for (int64_t k = 0; k < m && !bad; k++) {
         if (g[k].param < 0) continue;
-        int na = or_gate_n_angles(g[k].kind);
+        const int na = or_gate_n_angles(g[k].kind);
+        if (g[k].param + na > n_params) { bad = 1; break; }
+        const double base[2] = { params[g[k].param], na > 1 ? params[g[k].param + 1] : 0.0 };
         for (int a = 0; a < na; a++) {
-            int64_t idx = g[k].param + a;
-            if (idx >= n_params) { bad = 1; continue; }
-            double rk = shift_r(g[k].kind, a);
-            if (r[idx] != 0.0 && r[idx] != rk) bad = 1;
-            r[idx] = rk;
+            const double r = shift_r(g[k].kind, a);
+            double dE;
+            if (method == 0) {
+                const double d1 = M_PI / (4 * r), d2 = M_PI / (2 * r);
+                const double D1 = eval_moved(n, gg, k, m, params, base, a, d1, pauli, ref, work) -
+                                  eval_moved(n, gg, k, m, params, base, a, -d1, pauli, ref, work);
+                if (three_eigenvalues(&g[k], a)) {
+                    const double D2 = eval_moved(n, gg, k, m, params, base, a, d2, pauli, ref, work) -
+                                      eval_moved(n, gg, k, m, params, base, a, -d2, pauli, ref, work);
+                    dE = r * ((0.5 - 0.5 * sqrt(2.0)) * D2 + D1);
+                } else {
+                    dE = r * D1;
+                }
+            } else {
+                dE = (eval_moved(n, gg, k, m, params, base, a, h, pauli, ref, work) -
+                      eval_moved(n, gg, k, m, params, base, a, -h, pauli, ref, work)) / (2 * h);
+            }
+            gg[k] = g[k];
+            grad[g[k].param + a] += dE;
         }
     }
-    for (int64_t k = 0; k < n_params && !bad; k++) {
-        double d = h;
-        if (method == 0) {
-            if (r[k] == 0.0) { grad[k] = 0.0; continue; }  /* unused parameter */
-            d = M_PI / (4 * r[k]);
-        }
-        p[k] = params[k] + d;
-        double ep = cost_eval(n, g, m, p, pauli, ref, work);
-        p[k] = params[k] - d;
-        double em = cost_eval(n, g, m, p, pauli, ref, work);
-        p[k] = params[k];
-        grad[k] = method == 0 ? r[k] * (ep - em) : (ep - em) / (2 * h);
-    }
-    free(p);
-    free(r);
+    free(gg);
     free(work);
     return bad ? -1 : 0;
 }

@@ -470,6 +470,25 @@ def test_trajectory_draws_are_deterministic():
 # Gradients
 # ---------------------------------------------------------------------------
 
+def test_gradient_controlled_rotation_and_shared_parameter_closed_forms():
+    # controlled RY(t) with the control in |+>: <Z_target> = (1 + cos t) / 2,
+    # derivative -sin(t) / 2 (generator eigenvalues {-1/2, 0, 1/2}: the
+    # four-term rule); RY(t) twice on one qubit is RY(2t): <Z> = cos 2t,
+    # derivative -2 sin 2t (the occurrences' derivatives add)
+    for t in [-2.5, -0.4, 0.9, 2.2]:
+        gates = [W.Gate("H", 0), W.Gate("RY", 1, controls={0: 1}, angles=(t,), param=0)]
+        for method in ("shift", "fd"):
+            g = oracle.gradient(2, gates, np.array([t]), pauli="IZ", method=method, h=1e-5)
+            assert abs(g[0] + math.sin(t) / 2) < (1e-13 if method == "shift" else 1e-9)
+        gates = [W.Gate("RY", 0, angles=(t,), param=0), W.Gate("RY", 0, angles=(t,), param=0)]
+        g = oracle.gradient(1, gates, np.array([t]), pauli="Z", method="shift")
+        assert abs(g[0] + 2 * math.sin(2 * t)) < 1e-13
+        # controlled U_R(t) with control |+>: <Z> = (1 + cos 2t) / 2
+        gates = [W.Gate("H", 0), W.Gate("UR", 1, controls={0: 1}, angles=(t,), param=0)]
+        g = oracle.gradient(2, gates, np.array([t]), pauli="IZ", method="shift")
+        assert abs(g[0] + math.sin(2 * t)) < 1e-13
+
+
 def test_gradient_closed_forms_one_qubit():
     # RY(t)|0>: <Z> = cos t;  U_R(t)|0>: <Z> = cos 2t
     for t in [-2.0, -0.3, 0.7, 2.9]:
