@@ -387,6 +387,17 @@ typedef struct {
 qs_status qs_adjoint_grad(qs_state *s, const qs_gate *g, size_t m, const double *params, size_t n_params,
                           const qs_observable *obs, double *value, double *grad);
 
+/* qs_adjoint_grad with execution options (NULL: defaults).  By default the
+ * reverse sweep is fused: consecutive steps whose targets lie in a tile of
+ * 2^12 (complex64) / 2^11 (complex128) amplitudes run tile by tile with psi
+ * and lambda in shared memory (one HBM round trip of both vectors per group
+ * of steps); opts->no_fusion = 1 runs one sweep of both vectors per step.
+ * Registers of fewer than 6 qubits always use the per-step sweep.  The two
+ * paths give the same gradient up to rounding (the order of the partial sums
+ * differs). */
+qs_status qs_adjoint_grad_ex(qs_state *s, const qs_gate *g, size_t m, const double *params, size_t n_params,
+                             const qs_observable *obs, double *value, double *grad, const qs_exec_opts *opts);
+
 /* --------------------------------------------------------------------- */
 /* Host copies (checkpoint / restore)                                      */
 /* --------------------------------------------------------------------- */

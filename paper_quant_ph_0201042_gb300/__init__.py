@@ -123,6 +123,9 @@ _SIGS = {
     "qs_adjoint_grad": [ctypes.c_void_p, ctypes.POINTER(QsGate), ctypes.c_size_t, ctypes.POINTER(ctypes.c_double),
                         ctypes.c_size_t, ctypes.POINTER(QsObservable), ctypes.POINTER(ctypes.c_double),
                         ctypes.POINTER(ctypes.c_double)],
+    "qs_adjoint_grad_ex": [ctypes.c_void_p, ctypes.POINTER(QsGate), ctypes.c_size_t, ctypes.POINTER(ctypes.c_double),
+                           ctypes.c_size_t, ctypes.POINTER(QsObservable), ctypes.POINTER(ctypes.c_double),
+                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(QsExecOpts)],
     "qs_copy_out": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t],
     "qs_copy_in": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t],
 }
@@ -433,11 +436,11 @@ def batch_groups(batch) -> list:
 
 
 def adjoint_grad(work: "State", gates: Sequence, params, pauli: Optional[str] = None,
-                 ref: Optional["State"] = None):
-    """(E, dE/dparams) by the adjoint reverse sweep (qs_adjoint_grad).  E is
+                 ref: Optional["State"] = None, fuse: bool = True):
+    """(E, dE/dparams) by the adjoint reverse sweep (qs_adjoint_grad_ex).  E is
     <psi|pauli|psi> or, with ref, |<ref|psi>|^2; psi is the circuit applied to
     |0...0> in `work` with gate angles taken from params by each gate's param
-    index."""
+    index.  fuse=False runs one sweep of both vectors per step."""
     arr = gates_to_abi(gates)
     prm = np.ascontiguousarray(np.asarray(params, dtype=np.float64).reshape(-1))
     grad = np.zeros(max(1, prm.size))
@@ -449,9 +452,10 @@ def adjoint_grad(work: "State", gates: Sequence, params, pauli: Optional[str] = 
     else:
         obs.kind = OBS_PAULI
         obs.pauli = pauli.encode()
-    check(lib().qs_adjoint_grad(work.handle, arr, len(gates), prm.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                                prm.size, ctypes.byref(obs), ctypes.byref(val),
-                                grad.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    opts = _opts(fuse)
+    check(lib().qs_adjoint_grad_ex(work.handle, arr, len(gates), prm.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                   prm.size, ctypes.byref(obs), ctypes.byref(val),
+                                   grad.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(opts)))
     return val.value, grad[:prm.size]
 
 

@@ -16,6 +16,15 @@
 // then double across threads; complex128: double throughout) and writes one
 // partial per angle; fixed-order reductions then give one sum per angle and
 // one per parameter.
+//
+// Fused sweep (default): the reverse steps are grouped into tile passes by
+// the fused planner's pass formation (steps whose targets lie in a tile of
+// 2^K amplitudes, controls anywhere; commuting steps may move ahead, which
+// leaves every gradient term unchanged because U_k then also commutes with
+// dU_j U_j^dagger).  A CTA loads the tile of psi and of lambda into shared
+// memory once, runs the pass's steps on it (gradient partial, then the
+// uncompute) and writes both tiles back: one HBM round trip of the two vectors
+// per pass instead of per step.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -55,7 +64,7 @@ template <typename R>
 __device__ __forceinline__ R rdot(cplx<R> a, cplx<R> b) { return a.x * b.x + a.y * b.y; }   // Re(conj(a) b)
 
 template <typename R>
-__device__ __forceinline__ cplx<R> cmat(const double *u, int k) { return mk<R>(R(u[2 * k]), R(u[2 * k + 1])); }
+__host__ __device__ __forceinline__ cplx<R> cmat(const double *u, int k) { return mk<R>(R(u[2 * k]), R(u[2 * k + 1])); }
 
 __device__ __forceinline__ double blk_sum(double v) {
     __shared__ double sh[THREADS / 32];
@@ -225,15 +234,265 @@ int kind_angles(int kind) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Fused reverse sweep
+// ---------------------------------------------------------------------------
+constexpr int AF_THREADS = 256;
+constexpr int AF_WARPS = AF_THREADS / 32;
+
+template <typename R>
+struct alignas(16) AdjFOp {    // one reverse step of a pass, tile-local form
+    int32_t mode;              // 0 pair op, 1 C-NOT-like exchange, 2 diagonal on a tile bit, 3 diagonal on an outer bit
+    int32_t tpos;              // tile-local target bit (modes 0-2) or global target bit (mode 3)
+    uint32_t cm, cv;           // controls on tile bits (tile-local positions)
+    uint64_t om, ov;           // controls on outer bits (global positions)
+    int32_t nang;              // generators accumulated (0, 1, 2)
+    int32_t acc;               // first accumulator of this pass used by the step
+    int32_t slot0, slot1;      // global partial-sum slots of the generators
+    cplx<R> ui[4];             // U^dagger
+    cplx<R> g0[4], g1[4];      // generators dU U^dagger
+};
+
+template <typename R>
+struct AdjFPass {
+    const AdjFOp<R> *ops;
+    uint64_t tiles;
+    int32_t nops, K, nacc;
+    uint8_t tile_pos[16];
+};
+
+template <typename R>
+__device__ __forceinline__ double warp_sum_d(R v) {
+    double d = double(v);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+    return d;
+}
+
+template <typename R>
+__device__ __forceinline__ R pair_grad(const cplx<R> *g, cplx<R> px, cplx<R> py, cplx<R> lx, cplx<R> ly) {
+    return rdot<R>(lx, cmad2<R>(g[0], px, g[1], py)) + rdot<R>(ly, cmad2<R>(g[2], px, g[3], py));
+}
+
+template <typename R>
+__global__ void __launch_bounds__(AF_THREADS, 2) k_adj_pass(cplx<R> *__restrict__ psi, cplx<R> *__restrict__ lam,
+                                                            const __grid_constant__ AdjFPass<R> P,
+                                                            double *__restrict__ part) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int K = P.K;
+    const uint32_t T = 1u << K;
+    cplx<R> *sp = reinterpret_cast<cplx<R> *>(smraw);
+    cplx<R> *sl = sp + T;
+    double *sacc = reinterpret_cast<double *>(sl + T);                        // nacc x AF_WARPS
+    AdjFOp<R> *sops = reinterpret_cast<AdjFOp<R> *>(sacc + P.nacc * AF_WARPS);   // the pass's steps
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    for (int k = tid; k < P.nacc * AF_WARPS; k += AF_THREADS) sacc[k] = 0.0;
+    {
+        const uint4 *src = reinterpret_cast<const uint4 *>(P.ops);
+        uint4 *dst = reinterpret_cast<uint4 *>(sops);
+        const int words = P.nops * int(sizeof(AdjFOp<R>) / 16);
+        for (int k = tid; k < words; k += AF_THREADS) dst[k] = src[k];
+    }
+    for (uint64_t tile = blockIdx.x; tile < P.tiles; tile += gridDim.x) {
+        uint64_t base = tile;
+        for (int k = 0; k < K; ++k) {
+            const uint64_t low = (uint64_t(1) << P.tile_pos[k]) - 1;
+            base = ((base & ~low) << 1) | (base & low);
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (uint32_t e = tid; e < T; e += AF_THREADS) {
+            uint64_t gi = base;
+            for (int k = 0; k < K; ++k)
+                if ((e >> k) & 1) gi |= uint64_t(1) << P.tile_pos[k];
+            sp[e] = psi[gi];
+            sl[e] = lam[gi];
+        }
+        __syncthreads();
+        for (int k = 0; k < P.nops; ++k) {
+            const AdjFOp<R> &os = sops[k];
+            const uint64_t om = os.om, ov = os.ov;
+            if ((base & om) != ov) continue;            // the same for the whole tile
+            const int mode = os.mode, tpos = os.tpos, nang = os.nang;
+            const uint32_t cm = os.cm, cv = os.cv;
+            const cplx<R> u0 = os.ui[0], u1 = os.ui[1], u2 = os.ui[2], u3 = os.ui[3];
+            const cplx<R> a0g[4] = {os.g0[0], os.g0[1], os.g0[2], os.g0[3]};
+            const cplx<R> a1g[4] = {os.g1[0], os.g1[1], os.g1[2], os.g1[3]};
+            R a0 = R(0), a1 = R(0);
+            if (mode <= 1) {
+                const uint32_t tb = 1u << tpos;
+#pragma unroll 4
+                for (uint32_t p = tid; p < T / 2; p += AF_THREADS) {
+                    const uint32_t i0 = ((p >> tpos) << (tpos + 1)) | (p & (tb - 1));
+                    if ((i0 & cm) != cv) continue;
+                    const uint32_t i1 = i0 | tb;
+                    const cplx<R> px = sp[i0], py = sp[i1], lx = sl[i0], ly = sl[i1];
+                    if (nang > 0) {
+                        a0 += pair_grad<R>(a0g, px, py, lx, ly);
+                        if (nang > 1) a1 += pair_grad<R>(a1g, px, py, lx, ly);
+                    }
+                    if (mode == 1) {
+                        sp[i0] = py; sp[i1] = px; sl[i0] = ly; sl[i1] = lx;
+                    } else {
+                        sp[i0] = cmad2<R>(u0, px, u1, py); sp[i1] = cmad2<R>(u2, px, u3, py);
+                        sl[i0] = cmad2<R>(u0, lx, u1, ly); sl[i1] = cmad2<R>(u2, lx, u3, ly);
+                    }
+                }
+            } else {
+                const bool outer_one = mode == 3 && ((base >> tpos) & 1);
+#pragma unroll 4
+                for (uint32_t e = tid; e < T; e += AF_THREADS) {
+                    if ((e & cm) != cv) continue;
+                    const bool one = mode == 2 ? ((e >> tpos) & 1) : outer_one;
+                    const cplx<R> x = sp[e], l = sl[e];
+                    if (nang > 0) {
+                        a0 += rdot<R>(l, cmul<R>(one ? a0g[3] : a0g[0], x));
+                        if (nang > 1) a1 += rdot<R>(l, cmul<R>(one ? a1g[3] : a1g[0], x));
+                    }
+                    const cplx<R> d = one ? u3 : u0;
+                    sp[e] = cmul<R>(d, x);
+                    sl[e] = cmul<R>(d, l);
+                }
+            }
+            if (nang > 0) {
+                const double s0 = warp_sum_d<R>(a0);
+                if (lane == 0) sacc[os.acc * AF_WARPS + warp] += s0;
+                if (nang > 1) {
+                    const double s1 = warp_sum_d<R>(a1);
+                    if (lane == 0) sacc[(os.acc + 1) * AF_WARPS + warp] += s1;
+                }
+            }
+            __syncthreads();
+        }
+#pragma unroll 4
+        for (uint32_t e = tid; e < T; e += AF_THREADS) {
+            uint64_t gi = base;
+            for (int k = 0; k < K; ++k)
+                if ((e >> k) & 1) gi |= uint64_t(1) << P.tile_pos[k];
+            psi[gi] = sp[e];
+            lam[gi] = sl[e];
+        }
+    }
+    __syncthreads();
+    // one partial per generator slot and CTA
+    for (int k = 0; k < P.nops; ++k) {
+        const AdjFOp<R> &o = sops[k];
+        for (int a = 0; a < o.nang; ++a) {
+            if (tid < 32) {
+                double v = lane < AF_WARPS ? sacc[(o.acc + a) * AF_WARPS + lane] : 0.0;
+#pragma unroll
+                for (int q = 16; q > 0; q >>= 1) v += __shfl_xor_sync(0xffffffffu, v, q);
+                if (lane == 0) part[uint64_t(a == 0 ? o.slot0 : o.slot1) * gridDim.x + blockIdx.x] = v;
+            }
+        }
+    }
+}
+
 struct Buf {
     void *p = nullptr;
     cudaStream_t s = nullptr;
     ~Buf() { if (p) cudaFreeAsync(p, s); }
 };
 
+// at most ADJ_MAX_OPS steps per pass (the planner counts two budget units per op)
+constexpr int ADJ_MAX_OPS = 64;
+
+template <typename R>
+size_t adj_smem(int K, int nacc, int nops) {
+    return (sizeof(cplx<R>) << (K + 1)) + sizeof(double) * AF_WARPS * size_t(nacc) + sizeof(AdjFOp<R>) * size_t(nops);
+}
+
+// The fused reverse sweep over steps[] (in forward order; run last to first).
+template <typename R>
+cudaError_t fused_sweep(qs_state *s, const std::vector<AdjStep> &steps, const std::vector<HostOp> &hops,
+                        cplx<R> *psi, cplx<R> *lp, double *part, int grid, int K) {
+    const int n = s->n;
+    cudaStream_t st = s->stream;
+    // reverse steps as planner ops (SWAP already split into C-NOTs by the caller)
+    std::vector<HostOp> rev;
+    for (size_t j = steps.size(); j-- > 0;) {
+        HostOp o = hops[j];
+        o.step = int32_t(j);
+        if (steps[j].cls == AC_DIAG) o.cls = GC_DIAG;
+        else if (steps[j].cls == AC_X) o.cls = GC_X;
+        else o.cls = GC_GEN;
+        rev.push_back(o);
+    }
+    const int H = K - 5;
+    std::vector<PassGroup> groups = group_passes(n, H, 2 * ADJ_MAX_OPS, rev);
+    std::vector<AdjFOp<R>> flat;
+    std::vector<AdjFPass<R>> passes;
+    std::vector<size_t> offs;
+    for (const PassGroup &gp : groups) {
+        std::vector<int> tp = {0, 1, 2, 3, 4};
+        tp.insert(tp.end(), gp.high.begin(), gp.high.end());
+        std::sort(tp.begin(), tp.end());
+        int local[64];
+        for (int b = 0; b < 64; ++b) local[b] = -1;
+        for (int k = 0; k < K; ++k) local[tp[k]] = k;
+        AdjFPass<R> P;
+        std::memset(&P, 0, sizeof(P));
+        P.K = K;
+        P.tiles = uint64_t(1) << (n - K);
+        for (int k = 0; k < K; ++k) P.tile_pos[k] = uint8_t(tp[k]);
+        offs.push_back(flat.size());
+        int nacc = 0;
+        for (int j : gp.idx) {
+            const AdjStep &d = steps[size_t(j)];
+            const HostOp &o = hops[size_t(j)];
+            AdjFOp<R> f;
+            std::memset(&f, 0, sizeof(f));
+            const int b = o.bit;
+            if (d.cls == AC_DIAG) {
+                if (local[b] >= 0) { f.mode = 2; f.tpos = local[b]; }
+                else { f.mode = 3; f.tpos = b; }
+            } else {
+                if (local[b] < 0) return cudaErrorInvalidValue;   // the planner keeps targets in the tile
+                f.mode = d.cls == AC_X ? 1 : 0;
+                f.tpos = local[b];
+            }
+            for (int c = 0; c < n; ++c) {
+                if (!((o.cmask >> c) & 1)) continue;
+                const bool one = (o.cval >> c) & 1;
+                if (local[c] >= 0) { f.cm |= 1u << local[c]; if (one) f.cv |= 1u << local[c]; }
+                else { f.om |= uint64_t(1) << c; if (one) f.ov |= uint64_t(1) << c; }
+            }
+            f.nang = d.nang;
+            f.acc = nacc;
+            f.slot0 = d.slot0;
+            f.slot1 = d.slot1;
+            nacc += d.nang;
+            for (int e = 0; e < 4; ++e) {
+                f.ui[e] = cmat<R>(d.ui, e);
+                f.g0[e] = cmat<R>(d.g0, e);
+                f.g1[e] = cmat<R>(d.g1, e);
+            }
+            flat.push_back(f);
+        }
+        P.nops = int(gp.idx.size());
+        P.nacc = nacc;
+        passes.push_back(P);
+    }
+    void *dops = nullptr;
+    cudaError_t e = cudaMallocAsync(&dops, sizeof(AdjFOp<R>) * std::max<size_t>(1, flat.size()), st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(dops, flat.data(), sizeof(AdjFOp<R>) * flat.size(), cudaMemcpyHostToDevice, st);
+    size_t smem_max = 0;
+    for (const AdjFPass<R> &P : passes) smem_max = std::max(smem_max, adj_smem<R>(K, P.nacc, P.nops));
+    if (smem_max > adj_smem<R>(K, 2 * ADJ_MAX_OPS, ADJ_MAX_OPS)) e = cudaErrorInvalidValue;
+    for (size_t k = 0; k < passes.size() && e == cudaSuccess; ++k) {
+        AdjFPass<R> P = passes[k];
+        P.ops = static_cast<const AdjFOp<R> *>(dops) + offs[k];
+        k_adj_pass<R><<<unsigned(grid), AF_THREADS, adj_smem<R>(K, P.nacc, P.nops), st>>>(psi, lp, P, part);
+        e = cudaGetLastError();
+    }
+    cudaFreeAsync(dops, st);
+    return e;
+}
+
 template <typename R>
 qs_status run_adjoint(qs_state *s, const std::vector<qs_gate> &gg, size_t n_params, const qs_observable &obs,
-                      double *value, double *grad) {
+                      double *value, double *grad, bool fuse) {
     const int n = s->n;
     const uint64_t N = uint64_t(1) << n;
     cudaStream_t st = s->stream;
@@ -273,13 +532,32 @@ qs_status run_adjoint(qs_state *s, const std::vector<qs_gate> &gg, size_t n_para
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "adjoint launch");
-    // steps, slots
-    std::vector<AdjStep> steps(gg.size());
+    // steps, slots (a SWAP becomes three C-NOTs)
+    std::vector<AdjStep> steps;
+    std::vector<HostOp> hops;
     std::vector<std::pair<int, int>> slot_param;   // (param, slot)
-    for (size_t j = 0; j < gg.size(); ++j) {
-        HostOp o;
-        rc = synthesize(n, gg[j], o);
+    for (size_t jg = 0; jg < gg.size(); ++jg) {
+        HostOp og;
+        rc = synthesize(n, gg[jg], og);
         if (rc != QS_OK) return rc;
+        std::vector<HostOp> parts;
+        if (og.cls == GC_SWAP) {
+            HostOp x = og;
+            x.cls = GC_X;
+            x.kind = QS_GATE_X;
+            for (int k = 0; k < 8; ++k) x.u[k] = 0.0;
+            x.u[2] = 1.0; x.u[4] = 1.0;
+            HostOp c1 = x, c2 = x;
+            c1.bit = og.bit; c1.cmask = uint64_t(1) << og.bit2; c1.cval = uint64_t(1) << og.bit2;
+            c2.bit = og.bit2; c2.cmask = og.cmask | (uint64_t(1) << og.bit); c2.cval = og.cval | (uint64_t(1) << og.bit);
+            parts = {c1, c2, c1};
+        } else {
+            parts = {og};
+        }
+        for (const HostOp &o : parts) {
+        const size_t j = steps.size();
+        steps.emplace_back();
+        hops.push_back(o);
         AdjStep &d = steps[j];
         std::memset(&d, 0, sizeof(d));
         std::vector<int> pos;
@@ -302,23 +580,39 @@ qs_status run_adjoint(qs_state *s, const std::vector<qs_gate> &gg, size_t n_para
         std::sort(pos.begin(), pos.end());
         d.nfixed = int(pos.size());
         for (size_t k = 0; k < pos.size(); ++k) d.pos[k] = uint8_t(pos[k]);
-        if (gg[j].param >= 0) {
-            const int na = kind_angles(gg[j].kind);
+        if (gg[jg].param >= 0) {
+            const int na = kind_angles(gg[jg].kind);
             if (na == 0) return fail(QS_EUNSUPPORTED, "adjoint: a parameter on a gate kind without angles");
             for (int a = 0; a < na; ++a) {
-                const int pidx = gg[j].param + a;
+                const int pidx = gg[jg].param + a;
                 if (pidx >= int(n_params)) return fail(QS_EINVAL, "adjoint: parameter index beyond n_params");
                 double *g = a == 0 ? d.g0 : d.g1;
-                generator(gg[j].kind, a, gg[j].theta[0], gg[j].theta[1], g);
+                generator(gg[jg].kind, a, gg[jg].theta[0], gg[jg].theta[1], g);
                 const int slot = int(slot_param.size());
                 (a == 0 ? d.slot0 : d.slot1) = slot;
                 slot_param.push_back({pidx, slot});
             }
             d.nang = na;
         }
+        }
     }
     const int nslot = int(slot_param.size());
-    const int nblk = RED_BLOCKS;
+    // fused sweep: tiles of 2^K amplitudes (64 KiB per vector), one CTA per
+    // tile at a time, as many CTAs as fit
+    const int Kf = std::min(n, sizeof(R) == 4 ? 12 : 11);
+    const bool fused = fuse && n >= 6;
+    int nblk = RED_BLOCKS;
+    if (fused) {
+        // the largest pass: ADJ_MAX_OPS steps with two generators each
+        const size_t smem_max = adj_smem<R>(Kf, 2 * ADJ_MAX_OPS, ADJ_MAX_OPS);
+        cudaFuncSetAttribute(k_adj_pass<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_max));
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_adj_pass<R>, AF_THREADS, smem_max);
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        nblk = int(std::min<uint64_t>(uint64_t(1) << (n - Kf), uint64_t(std::max(sms, 1)) * std::max(occ, 1)));
+    }
     Buf part, ssum, dgrad, dfirst, dsteps;
     for (Buf *b : {&part, &ssum, &dgrad, &dfirst, &dsteps}) b->s = st;
     if (cudaMallocAsync(&part.p, sizeof(double) * std::max(1, nslot) * nblk, st) != cudaSuccess ||
@@ -347,9 +641,14 @@ qs_status run_adjoint(qs_state *s, const std::vector<qs_gate> &gg, size_t n_para
     // reverse sweep
     cplx<R> *psi = static_cast<cplx<R> *>(s->d);
     cplx<R> *lp = static_cast<cplx<R> *>(lam.p);
-    for (size_t j = steps.size(); j-- > 0;) {
-        k_adj<R><<<nblk, THREADS, 0, st>>>(psi, lp, n, static_cast<const AdjStep *>(dsteps.p) + j,
-                                           static_cast<double *>(part.p));
+    if (fused) {
+        e = fused_sweep<R>(s, steps, hops, psi, lp, static_cast<double *>(part.p), nblk, Kf);
+        if (e != cudaSuccess) return cuda_fail(e, "adjoint fused sweep");
+    } else {
+        for (size_t j = steps.size(); j-- > 0;) {
+            k_adj<R><<<nblk, THREADS, 0, st>>>(psi, lp, n, static_cast<const AdjStep *>(dsteps.p) + j,
+                                               static_cast<double *>(part.p));
+        }
     }
     if (nslot > 0) k_slot_sums<<<nslot, THREADS, 0, st>>>(static_cast<const double *>(part.p), nblk,
                                                           static_cast<double *>(ssum.p));
@@ -375,6 +674,13 @@ using namespace qs;
 
 extern "C" qs_status qs_adjoint_grad(qs_state *s, const qs_gate *g, size_t m, const double *params, size_t n_params,
                                      const qs_observable *obs, double *value, double *grad) {
+    return qs_adjoint_grad_ex(s, g, m, params, n_params, obs, value, grad, nullptr);
+}
+
+extern "C" qs_status qs_adjoint_grad_ex(qs_state *s, const qs_gate *g, size_t m, const double *params,
+                                        size_t n_params, const qs_observable *obs, double *value, double *grad,
+                                        const qs_exec_opts *opts) {
+    const bool fuse = !(opts && opts->no_fusion);
     if (!s || !obs || !value || (m > 0 && !g) || (n_params > 0 && (!params || !grad)))
         return fail(QS_EINVAL, "NULL argument");
     if (n_params > (size_t(1) << 30)) return fail(QS_ERANGE, "too many parameters");
@@ -395,6 +701,6 @@ extern "C" qs_status qs_adjoint_grad(qs_state *s, const qs_gate *g, size_t m, co
         if (x.param + std::max(na, 1) > int64_t(n_params)) return fail(QS_EINVAL, "gate parameter index beyond n_params");
         for (int a = 0; a < na; ++a) x.theta[a] = params[x.param + a];
     }
-    return s->dt == QS_C64 ? run_adjoint<float>(s, gg, n_params, *obs, value, grad)
-                           : run_adjoint<double>(s, gg, n_params, *obs, value, grad);
+    return s->dt == QS_C64 ? run_adjoint<float>(s, gg, n_params, *obs, value, grad, fuse)
+                           : run_adjoint<double>(s, gg, n_params, *obs, value, grad, fuse);
 }

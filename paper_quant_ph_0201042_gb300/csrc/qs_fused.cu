@@ -1086,6 +1086,20 @@ std::vector<PlannedPass> form_passes(int n, int H, int max_ops, const std::vecto
     return passes;
 }
 
+}  // namespace
+
+std::vector<PassGroup> group_passes(int n, int H, int max_ops, const std::vector<HostOp> &ops) {
+    std::vector<PlannedPass> pp = form_passes(n, H, max_ops, ops);
+    std::vector<PassGroup> out(pp.size());
+    for (size_t k = 0; k < pp.size(); ++k) {
+        out[k].high = pp[k].high;
+        for (const HostOp &o : pp[k].ops) out[k].idx.push_back(o.step);
+    }
+    return out;
+}
+
+namespace {
+
 template <typename R, int RB>
 qs_status build_fused(Plan *P, const std::vector<HostOp> &ops, int max_ops,
                       std::vector<PassDesc<R>> &out, std::vector<std::vector<FOp<R>>> &tables) {

@@ -159,6 +159,17 @@ int64_t traj_plan_launches(const TrajPlan *p);
 cudaError_t traj_plan_run(TrajPlan *p, float2 *states, uint32_t count, const TrajRec *recs, cudaStream_t st);
 void traj_plan_destroy(TrajPlan *p);
 std::string plan_describe(const Plan *p);
+
+// The fused planner's greedy pass formation, for other fused kernels: per
+// pass, its high tile bits (ascending; the five lowest index bits are always
+// in the tile) and the ops it runs, as their HostOp::step values, in order.
+// An op needs its target among the tile bits unless it is diagonal; controls
+// may be anywhere.  Ops move ahead of others only where they commute.
+struct PassGroup {
+    std::vector<int> high;
+    std::vector<int> idx;
+};
+std::vector<PassGroup> group_passes(int n, int H, int max_ops, const std::vector<HostOp> &ops);
 qs_dtype plan_dtype(const Plan *p);
 
 }  // namespace qs

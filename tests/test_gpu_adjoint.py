@@ -26,15 +26,16 @@ def perturbed(params, sigma, seed):
     return params + sigma * W.rng(seed).standard_normal(params.size)
 
 
+@pytest.mark.parametrize("fuse", [True, False])
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
-def test_ansatz_n10_pauli_against_parameter_shift(dtype):
+def test_ansatz_n10_pauli_against_parameter_shift(dtype, fuse):
     # the gradient workload at the oracle's size: 25 layers of RY, RZ and a
     # C-NOT ladder on 10 qubits (500 angles), observable <Z_0>
     n = 10
     gates, params = W.ansatz_circuit(n, 25, seed=4)
     pauli = "Z" + "I" * (n - 1)
     work = qs.State(n, dtype)
-    val, grad = qs.adjoint_grad(work, gates, params, pauli=pauli)
+    val, grad = qs.adjoint_grad(work, gates, params, pauli=pauli, fuse=fuse)
     want_val = oracle.cost(n, gates, params, pauli=pauli)
     want = oracle.gradient(n, gates, params, pauli=pauli, method="shift")
     assert abs(val - want_val) < GTOL[dtype]
@@ -43,8 +44,9 @@ def test_ansatz_n10_pauli_against_parameter_shift(dtype):
     assert np.max(np.abs(grad - fd)) < GTOL[dtype] + 1e-7
 
 
+@pytest.mark.parametrize("fuse", [True, False])
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
-def test_ansatz_n10_fidelity_to_noiseless_output(dtype):
+def test_ansatz_n10_fidelity_to_noiseless_output(dtype, fuse):
     # the fidelity to the noiseless output, differentiated with respect to
     # every (deviated) angle: d/dx F(theta + x) = dF/dtheta at theta + x
     n = 10
@@ -53,7 +55,7 @@ def test_ansatz_n10_fidelity_to_noiseless_output(dtype):
     x = perturbed(params, 0.05, 6)
     ref = qs.State(n, dtype).from_numpy(ideal)
     work = qs.State(n, dtype)
-    val, grad = qs.adjoint_grad(work, gates, x, ref=ref)
+    val, grad = qs.adjoint_grad(work, gates, x, ref=ref, fuse=fuse)
     want_val = oracle.cost(n, gates, x, ref=ideal)
     want = oracle.gradient(n, gates, x, ref=ideal, method="shift")
     assert abs(val - want_val) < GTOL[dtype]
@@ -81,9 +83,48 @@ def test_urp1_and_controlled_parameters():
     want = oracle.gradient(n, gates, params, pauli=pauli, method="shift")
     assert np.max(np.abs(want)) > 1e-2
     for dtype in ("c128", "c64"):
+        for fuse in (True, False):
+            work = qs.State(n, dtype)
+            val, grad = qs.adjoint_grad(work, gates, params, pauli=pauli, fuse=fuse)
+            assert np.max(np.abs(grad - want)) < GTOL[dtype], (dtype, fuse)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("n", [13, 14])
+def test_fused_sweep_every_gate_kind(dtype, n):
+    # several tiles: parameterised gates of every differentiable kind with
+    # controls inside and outside the tile, diagonal gates on outer bits,
+    # SWAPs and C-NOTs, two gates sharing a parameter; fused and per-step
+    # sweeps against the oracle's parameter-shift rule
+    r = W.rng(300 + n)
+    kinds = ["RY", "RZ", "UR", "UP1", "UP2", "URP1"]
+    gates, k = W.hadamard_layer(n), 0
+    for layer in range(4):
+        for q in range(n):
+            kind = kinds[int(r.integers(len(kinds)))]
+            ctr = {}
+            if r.random() < 0.3:
+                c = int(r.choice([x for x in range(n) if x != q]))
+                ctr[c] = int(r.integers(2))
+            na = 2 if kind == "URP1" else 1
+            gates.append(W.Gate(kind, q, controls=ctr, angles=(0.0,) * na, param=k))
+            k += na
+        for q in range(0, n - 1, 2):
+            gates.append(W.Gate("X", q + 1, controls={q: 1}))
+        a, b = (int(v) for v in r.choice(n, size=2, replace=False))
+        gates.append(W.Gate("SWAP", a, target2=b))
+    g0 = gates[n]                                               # a second gate on the first gate's parameter(s)
+    gates.append(W.Gate(g0.kind, (g0.target + 3) % n, angles=g0.angles, param=g0.param))
+    params = r.uniform(-math.pi, math.pi, size=k)
+    pauli = "".join(r.choice(list("IXYZ"), size=n))
+    want = oracle.gradient(n, gates, params, pauli=pauli, method="shift")
+    want_val = oracle.cost(n, gates, params, pauli=pauli)
+    assert np.max(np.abs(want)) > 1e-3
+    for fuse in (True, False):
         work = qs.State(n, dtype)
-        val, grad = qs.adjoint_grad(work, gates, params, pauli=pauli)
-        assert np.max(np.abs(grad - want)) < GTOL[dtype], dtype
+        val, grad = qs.adjoint_grad(work, gates, params, pauli=pauli, fuse=fuse)
+        assert abs(val - want_val) < GTOL[dtype], fuse
+        assert np.max(np.abs(grad - want)) < GTOL[dtype] * 4, (fuse, np.max(np.abs(grad - want)))
 
 
 def test_autograd_function_matches():
