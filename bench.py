@@ -475,9 +475,15 @@ def main():
             e2e_step()
         torch.cuda.synchronize()
         dt = max_over_ranks((time.perf_counter() - t0) / k, dist)
+        # the device-to-host copy alone (what the host link adds to the step)
+        t1 = time.perf_counter()
+        qs.check(qs.lib().qs_copy_out(state.handle, hbuf.ctypes.data_as(ctypes.c_void_p), hbuf.nbytes))
+        tc = time.perf_counter() - t1
         line["e2e"] = {"value": world * upd / dt, "unit": "amp-updates/s",
                        "h2d_bytes_per_step": ctypes.sizeof(garr), "d2h_bytes_per_step": hbuf.nbytes,
-                       "ms_per_step": dt * 1e3, "steps": k}
+                       "ms_per_step": dt * 1e3, "steps": k,
+                       "d2h_copy_ms": tc * 1e3, "d2h_gbs": hbuf.nbytes / tc / 1e9,
+                       "host_buffer_pinned": bool(host.is_pinned())}
         del host
 
     if not args.no_secondary and rank == 0:
