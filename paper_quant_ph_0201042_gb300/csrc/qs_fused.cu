@@ -391,7 +391,8 @@ __global__ void __launch_bounds__(32 << QS_MAX_WB, 1) k_fused(cplx<R> *__restric
 struct alignas(16) POp {
     uint8_t type, cls, tsel, tpos;
     uint8_t rmask, rval;
-    uint16_t pad0;
+    uint8_t fast;          // 1: uncontrolled general gate on a register slot (no trajectory record)
+    uint8_t pad0;
     uint32_t pad1;
     uint16_t tmask, tval;
     uint64_t omask, oval;
@@ -586,7 +587,22 @@ __global__ void __launch_bounds__(32 << QS_WB64, QS_FUSED_MINBLOCKS) k_fused_c64
         for (int k = 0; k < nops; ++k) {
             const POp &op = sops[k];
             const uint4 *q = reinterpret_cast<const uint4 *>(&op);
-            const uint4 hd = q[0], oc = q[1];
+            const uint4 hd = q[0];
+            if (!TRAJ && ((hd.y >> 16) & 0xff)) {
+                // uncontrolled general gate on register slot tpos: no predicate,
+                // no class dispatch
+                const float4 f0 = reinterpret_cast<const float4 *>(q)[2], f1 = reinterpret_cast<const float4 *>(q)[3];
+                const Mat4<float> mf = {make_float2(f0.x, f0.y), make_float2(f0.z, f0.w), make_float2(f1.x, f1.y),
+                                        make_float2(f1.z, f1.w)};
+                const int tp = hd.x >> 24;
+                if (tp == 0) s_gen<0, false, NA>(v, mf, xm, 0, 0);
+                else if (tp == 1) s_gen<1, false, NA>(v, mf, xm, 0, 0);
+                else if (tp == 2) s_gen<2, false, NA>(v, mf, xm, 0, 0);
+                else if (tp == 3) s_gen<3, false, NA>(v, mf, xm, 0, 0);
+                else s_gen<(RB64 > 4 ? 4 : 0), false, NA>(v, mf, xm, 0, 0);
+                continue;
+            }
+            const uint4 oc = q[1];
             const int type = hd.x & 0xff, cls = (hd.x >> 8) & 0xff, tsel = (hd.x >> 16) & 0xff,
                       tpos = hd.x >> 24;
             const int rm = hd.y & 0xff, rv = (hd.y >> 8) & 0xff;
@@ -1224,6 +1240,8 @@ void convert_c64(const PassDesc<float> &D, const std::vector<FOp<float>> &ops, P
         q.type = f.type; q.cls = f.cls; q.tsel = f.tsel; q.tpos = f.tpos;
         q.rmask = f.rmask; q.rval = f.rval; q.tmask = f.tmask; q.tval = f.tval;
         q.omask = f.omask; q.oval = f.oval;
+        q.fast = (f.type == OP_REG && f.cls != GC_X && f.cls != GC_HB && f.rmask == 0 && f.tmask == 0 &&
+                  f.omask == 0) ? 1 : 0;
         if (f.type == OP_XPOSE) {
             // position of each high tile bit in the old tile order
             // (register index bits above the warp bits, warp bits above the lanes)
