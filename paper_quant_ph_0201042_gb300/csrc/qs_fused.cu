@@ -391,7 +391,8 @@ __global__ void __launch_bounds__(32 << QS_MAX_WB, 1) k_fused(cplx<R> *__restric
 struct alignas(16) POp {
     uint8_t type, cls, tsel, tpos;
     uint8_t rmask, rval;
-    uint8_t fast;          // 1: uncontrolled general gate on a register slot (no trajectory record)
+    uint8_t fast;          // state-vector fast paths: 1 uncontrolled general gate on a register slot,
+                           // 2 X deferred into the index mask, 3 uncontrolled general gate on a lane bit
     uint8_t pad0;
     uint32_t pad1;
     uint16_t tmask, tval;
@@ -588,18 +589,38 @@ __global__ void __launch_bounds__(32 << QS_WB64, QS_FUSED_MINBLOCKS) k_fused_c64
             const POp &op = sops[k];
             const uint4 *q = reinterpret_cast<const uint4 *>(&op);
             const uint4 hd = q[0];
-            if (!TRAJ && ((hd.y >> 16) & 0xff)) {
-                // uncontrolled general gate on register slot tpos: no predicate,
-                // no class dispatch
+            const int fast = TRAJ ? 0 : int((hd.y >> 16) & 0xff);
+            if (fast) {
+                // the common cases without the general dispatch: no predicate
+                // work and no class tests
+                const int tp = hd.x >> 24;
+                if (fast == 2) {
+                    const uint4 oc = q[1];
+                    const uint64_t omask = uint64_t(oc.x) | (uint64_t(oc.y) << 32);
+                    const uint64_t oval = uint64_t(oc.z) | (uint64_t(oc.w) << 32);
+                    const bool ok = ((tl & (hd.w & 0xffff)) == (hd.w >> 16)) && ((base & omask) == oval);
+                    xm ^= ok ? (1u << tp) : 0u;
+                    continue;
+                }
                 const float4 f0 = reinterpret_cast<const float4 *>(q)[2], f1 = reinterpret_cast<const float4 *>(q)[3];
                 const Mat4<float> mf = {make_float2(f0.x, f0.y), make_float2(f0.z, f0.w), make_float2(f1.x, f1.y),
                                         make_float2(f1.z, f1.w)};
-                const int tp = hd.x >> 24;
-                if (tp == 0) s_gen<0, false, NA>(v, mf, xm, 0, 0);
-                else if (tp == 1) s_gen<1, false, NA>(v, mf, xm, 0, 0);
-                else if (tp == 2) s_gen<2, false, NA>(v, mf, xm, 0, 0);
-                else if (tp == 3) s_gen<3, false, NA>(v, mf, xm, 0, 0);
-                else s_gen<(RB64 > 4 ? 4 : 0), false, NA>(v, mf, xm, 0, 0);
+                if (fast == 1) {
+                    if (tp == 0) s_gen<0, false, NA>(v, mf, xm, 0, 0);
+                    else if (tp == 1) s_gen<1, false, NA>(v, mf, xm, 0, 0);
+                    else if (tp == 2) s_gen<2, false, NA>(v, mf, xm, 0, 0);
+                    else if (tp == 3) s_gen<3, false, NA>(v, mf, xm, 0, 0);
+                    else s_gen<(RB64 > 4 ? 4 : 0), false, NA>(v, mf, xm, 0, 0);
+                } else {
+                    const int m = 1 << tp;
+                    const bool hi = (lane >> tp) & 1;
+                    const float2 cs = hi ? mf.u11 : mf.u00, co = hi ? mf.u10 : mf.u01;
+#pragma unroll
+                    for (int j = 0; j < NA; ++j) {
+                        const float2 o = shfl<float>(v[j], m);
+                        v[j] = cmad2<float>(cs, v[j], co, o);
+                    }
+                }
                 continue;
             }
             const uint4 oc = q[1];
@@ -1240,8 +1261,14 @@ void convert_c64(const PassDesc<float> &D, const std::vector<FOp<float>> &ops, P
         q.type = f.type; q.cls = f.cls; q.tsel = f.tsel; q.tpos = f.tpos;
         q.rmask = f.rmask; q.rval = f.rval; q.tmask = f.tmask; q.tval = f.tval;
         q.omask = f.omask; q.oval = f.oval;
-        q.fast = (f.type == OP_REG && f.cls != GC_X && f.cls != GC_HB && f.rmask == 0 && f.tmask == 0 &&
-                  f.omask == 0) ? 1 : 0;
+        q.fast = 0;
+        if (f.type == OP_REG && f.cls != GC_X && f.cls != GC_HB && f.rmask == 0 && f.tmask == 0 && f.omask == 0)
+            q.fast = 1;
+        else if (f.type == OP_REG && f.cls == GC_X && f.rmask == 0 && (f.tmask & 31u) == 0)
+            q.fast = 2;
+        else if (f.type == OP_LANE && f.cls != GC_X && f.cls != GC_HB && f.rmask == 0 && f.tmask == 0 &&
+                 f.omask == 0)
+            q.fast = 3;
         if (f.type == OP_XPOSE) {
             // position of each high tile bit in the old tile order
             // (register index bits above the warp bits, warp bits above the lanes)
