@@ -589,7 +589,11 @@ __global__ void __launch_bounds__(32 << QS_WB64, QS_FUSED_MINBLOCKS) k_fused_c64
             const POp &op = sops[k];
             const uint4 *q = reinterpret_cast<const uint4 *>(&op);
             const uint4 hd = q[0];
-            const int fast = TRAJ ? 0 : int((hd.y >> 16) & 0xff);
+            // trajectory mode: an uncontrolled op's matrix is the trajectory's
+            // record; the deferred C-NOT path is skipped there (its control
+            // values change with the trajectory's Pauli frame)
+            int fast = int((hd.y >> 16) & 0xff);
+            if (TRAJ && fast == 2) fast = 0;
             if (fast) {
                 // the common cases without the general dispatch: no predicate
                 // work and no class tests
@@ -602,7 +606,8 @@ __global__ void __launch_bounds__(32 << QS_WB64, QS_FUSED_MINBLOCKS) k_fused_c64
                     xm ^= ok ? (1u << tp) : 0u;
                     continue;
                 }
-                const float4 f0 = reinterpret_cast<const float4 *>(q)[2], f1 = reinterpret_cast<const float4 *>(q)[3];
+                const float4 *cs4 = TRAJ ? reinterpret_cast<const float4 *>(srec[k].u) : reinterpret_cast<const float4 *>(q) + 2;
+                const float4 f0 = cs4[0], f1 = cs4[1];
                 const Mat4<float> mf = {make_float2(f0.x, f0.y), make_float2(f0.z, f0.w), make_float2(f1.x, f1.y),
                                         make_float2(f1.z, f1.w)};
                 if (fast == 1) {
