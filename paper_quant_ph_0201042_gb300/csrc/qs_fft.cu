@@ -173,22 +173,41 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) k_fft_pass(cplx<R> *__restrict
     const uint64_t m1 = (uint64_t(1) << P.s1) - 1, m2 = (uint64_t(1) << P.s2) - 1;
     const int d1b = P.s1 - P.r1, d2b = P.s2 - P.r2;     // digit bottoms relative to lo
 
-    for (uint64_t tile = blockIdx.x; tile < P.tiles; tile += gridDim.x) {
-        uint64_t base = tile;
+    // Tiles are loaded with cp.async into the shared-memory transpose buffer,
+    // in layout A at positions lane | warp << 5 | j << (5 + WB): each thread
+    // copies the 2^RB amplitudes it will hold and later reads only those, so
+    // its own wait suffices.  The copy of the next tile is issued as soon as
+    // the current tile's transpose has been read, and overlaps the rest of
+    // its work (digits 2 and 3, twiddles, the store).
+    auto tile_base = [&](uint64_t t) {
+        uint64_t b = t;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const uint64_t low = (uint64_t(1) << P.tile_pos[k]) - 1;
-            base = ((base & ~low) << 1) | (base & low);
+            b = ((b & ~low) << 1) | (b & low);
         }
-        cplx<R> v[NA];
+        return b;
+    };
+    auto issue_tile = [&](uint64_t b) {
 #pragma unroll
         for (int j = 0; j < NA; ++j) {
-            uint64_t o = base | offA;
+            uint64_t o = b | offA;
 #pragma unroll
             for (int r = 0; r < RB; ++r)
                 if ((j >> r) & 1) o |= uint64_t(1) << P.hpos[WB + r];
-            v[j] = a[o];
+            const uint32_t sa = uint32_t(__cvta_generic_to_shared(&sm[lane | (warp << 5) | (uint32_t(j) << (5 + WB))]));
+            asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(sa), "l"(a + o), "n"(int(sizeof(cplx<R>)))
+                         : "memory");
         }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    if (blockIdx.x < P.tiles) issue_tile(tile_base(blockIdx.x));
+    for (uint64_t tile = blockIdx.x; tile < P.tiles; tile += gridDim.x) {
+        const uint64_t base = tile_base(tile);
+        cplx<R> v[NA];
+        asm volatile("cp.async.wait_all;" ::: "memory");
+#pragma unroll
+        for (int j = 0; j < NA; ++j) v[j] = sm[lane | (warp << 5) | (uint32_t(j) << (5 + WB))];
         // digit 1: layout-A registers [0, r1)
         if (P.r1 > 0) {
             const uint64_t t0 = ((base | offA) >> lo) & m1 & ((uint64_t(1) << d1b) - 1);
@@ -201,6 +220,8 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) k_fft_pass(cplx<R> *__restrict
         __syncthreads();
 #pragma unroll
         for (int j = 0; j < NA; ++j) v[j] = sm[lane | (uint32_t(j) << 5) | (warp << (5 + RB))];
+        __syncthreads();
+        if (tile + gridDim.x < P.tiles) issue_tile(tile_base(tile + gridDim.x));
         // digit 2: layout-B registers [0, r2)
         if (P.r2 > 0) {
             const uint64_t t0 = ((base | offB) >> lo) & m2 & ((uint64_t(1) << d2b) - 1);
