@@ -93,3 +93,23 @@ def test_gate_struct_layout():
     assert g.kind == 5 and g.t == 3 and g.param == 7
     assert g.ctrl_mask == (1 << 1) | (1 << 5) and g.ctrl_val == 1 << 1
     assert g.theta[0] == 0.25
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    # no CPU fallback: without libqsim.so every entry point raises
+    monkeypatch.setattr(qs, "LIB_PATH", str(tmp_path / "absent.so"))
+    monkeypatch.setattr(qs, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        qs.lib()
+    with pytest.raises(RuntimeError, match="not built|no CUDA device"):
+        qs.State(4, "c64")
+
+
+def test_plans_schedule_fewer_transposes_than_program_order(libpath):
+    # the list scheduler keeps a pass's ops within their commutation freedom
+    # and needs fewer transposes than program order would
+    import re
+    d = qs.Plan(28, "c64", W.random_circuit(28, 40, seed=20260515)).describe()
+    xp = sum(int(v) for v in re.findall(r"xpose=(\d+)", d))
+    passes = len(re.findall(r"^pass ", d, flags=re.M))
+    assert passes > 0 and xp < 1.6 * passes, (xp, passes)
