@@ -174,7 +174,8 @@ def cpu_baseline(dtype, budget_s=20.0, n=None):
     return {"value": upd / dt, "unit": "amp-updates/s", "cores": oracle.num_threads(),
             "kind": "oracle",
             "sample": "first %d of %d gates of the workload at n=%d (complex128, OpenMP rows), %.1f s"
-                      % (done, len(gates), n, dt)}
+                      % (done, len(gates), n, dt),
+            "sample_seconds": dt, "full_step_updates": amp_updates(n, gates)}
 
 
 def run_reference(args, rank, world):
@@ -192,7 +193,11 @@ def run_reference(args, rank, world):
     line = {
         "impl": "reference", "metric": "amp-updates/s", "value": val, "unit": "amp-updates/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        # each timed step is a bounded sample of the workload; ms_per_step is
+        # one full step at the measured rate
+        "ms_per_step": base["full_step_updates"] / val * 1e3,
+        "sample_ms_per_step": statistics.median([s["sample_seconds"] for s in steps]) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic", "config": workload_config(args, world),
         "cpu_baseline": {"value": val, "unit": "amp-updates/s", "cores": base["cores"],
                          "kind": "oracle", "sample": base["sample"]},
@@ -492,7 +497,8 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         del state
         torch.cuda.empty_cache()
-        line["cpu_baseline"] = cpu_baseline(args.dtype)
+        cb = cpu_baseline(args.dtype)
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
