@@ -187,3 +187,21 @@ def test_adjoint_n26_full_size():
             shift = (fn(pp) - fn(pm)) / 2
             assert abs(fd - shift) < 1e-6, (k, fd, shift)
             assert abs(grad[k] - shift) < tol, (k, grad[k], shift)
+
+
+def test_no_parameters_and_unused_parameters():
+    # a circuit without parameters: the value only; parameters no gate uses
+    # get a zero derivative
+    n = 12
+    gates = W.random_circuit(n, 2, seed=3)
+    work = qs.State(n, "c64")
+    val, grad = qs.adjoint_grad(work, gates, np.zeros(0), pauli="Z" * n)
+    assert grad.size == 0
+    assert abs(val - oracle.cost(n, gates, np.zeros(0), pauli="Z" * n)) < 1e-5
+    g2, p2 = W.ansatz_circuit(n, 2, seed=4)
+    params = np.concatenate([p2, [0.3, -0.7]])            # two trailing unused parameters
+    for fuse in (True, False):
+        val, grad = qs.adjoint_grad(qs.State(n, "c128"), g2, params, pauli="Z" + "I" * (n - 1), fuse=fuse)
+        assert grad.size == params.size and grad[-1] == 0.0 and grad[-2] == 0.0
+        want = oracle.gradient(n, g2, params, pauli="Z" + "I" * (n - 1), method="shift")
+        assert np.max(np.abs(grad - want)) < 1e-9

@@ -215,3 +215,20 @@ def test_gate_flags_period_finding_qft(n, fuse):
     # a noiseless run with the flags is the exact periodic-state QFT: 2^r peaks
     m0, s0 = qs.run_trajectories(groups, 0.0, 0.0, seed, dtype="c64", fuse=fuse)
     assert np.all(s0 == 0) and np.max(np.abs(m0 - 1)) < 1e-5
+
+
+def test_empty_and_degenerate_groups():
+    # a group without trajectories contributes nothing; a group without gates
+    # keeps every trajectory at its basis state (fidelity 1, probability of x0
+    # 1) and draws no flips (flips follow gate steps)
+    n = 11
+    x0 = np.array([3, 5, 7], np.uint64)
+    groups = [{"n": n, "gates": W.noisy_synthesis(W.qft_circuit(n)), "x0": np.zeros(0, np.uint64), "first": 0},
+              {"n": n, "gates": [], "x0": x0, "first": 10},
+              {"n": n, "gates": [], "x0": x0, "first": 20, "metric": "prob", "target": 5}]
+    for fuse in (True, False):
+        met, st = qs.run_trajectories(groups, 0.5, 0.1, seed=3, dtype="c64", fuse=fuse)
+        assert met.size == 6
+        assert np.max(np.abs(met[:3] - 1)) < 1e-6
+        assert np.allclose(met[3:], [0.0, 1.0, 0.0], atol=1e-6)
+        assert np.all(st == 0)
