@@ -28,6 +28,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <set>
 #include <vector>
 
 #include "qs_internal.cuh"
@@ -239,10 +240,13 @@ int kind_angles(int kind) {
 // ---------------------------------------------------------------------------
 constexpr int AF_THREADS = 256;
 constexpr int AF_WARPS = AF_THREADS / 32;
+// at most ADJ_MAX_OPS steps per pass (the planner counts two budget units per op)
+constexpr int ADJ_MAX_OPS = 64;
 
 template <typename R>
 struct alignas(16) AdjFOp {    // one reverse step of a pass, tile-local form
-    int32_t mode;              // 0 pair op, 1 C-NOT-like exchange, 2 diagonal on a tile bit, 3 diagonal on an outer bit
+    int32_t mode;              // 0 pair op, 1 C-NOT-like exchange, 2 diagonal on a tile bit, 3 diagonal on an
+                               // outer bit, 4 pair op with a real matrix and real generators
     int32_t tpos;              // tile-local target bit (modes 0-2) or global target bit (mode 3)
     uint32_t cm, cv;           // controls on tile bits (tile-local positions)
     uint64_t om, ov;           // controls on outer bits (global positions)
@@ -253,20 +257,27 @@ struct alignas(16) AdjFOp {    // one reverse step of a pass, tile-local form
     cplx<R> g0[4], g1[4];      // generators dU U^dagger
 };
 
+// A pass's steps come in runs: within a run every non-diagonal step has the
+// same tile-local target bit, so each thread keeps the same amplitude pairs
+// (psi and lambda, split on that bit) in registers for the whole run and the
+// tile goes through shared memory once per run instead of once per step.
 template <typename R>
 struct AdjFPass {
     const AdjFOp<R> *ops;
     uint64_t tiles;
-    int32_t nops, K, nacc;
+    int32_t nops, K, nacc, nrun;
     uint8_t tile_pos[16];
+    uint8_t run_len[ADJ_MAX_OPS];
+    uint8_t run_bit[ADJ_MAX_OPS];
 };
 
+// warp sum in the state's precision (the few FP64 units stay free for the
+// per-warp accumulators, which are double)
 template <typename R>
 __device__ __forceinline__ double warp_sum_d(R v) {
-    double d = double(v);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-    return d;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return double(v);
 }
 
 template <typename R>
@@ -274,10 +285,132 @@ __device__ __forceinline__ R pair_grad(const cplx<R> *g, cplx<R> px, cplx<R> py,
     return rdot<R>(lx, cmad2<R>(g[0], px, g[1], py)) + rdot<R>(ly, cmad2<R>(g[2], px, g[3], py));
 }
 
+// One step of a run on the thread's register pairs.  Pair steps act on the
+// run's bit (their controls exclude it); a diagonal step scales each element
+// by the entry its own target bit selects.  NA generators are accumulated.
+template <typename R, int NP, bool CHK>
+__device__ __forceinline__ void run_exchange(uint32_t cm, uint32_t cv, const bool (&ok)[NP], const uint32_t (&i0)[NP],
+                                             cplx<R> (&px)[NP], cplx<R> (&py)[NP], cplx<R> (&lx)[NP],
+                                             cplx<R> (&ly)[NP]) {
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+        if (!ok[j] || (CHK && (i0[j] & cm) != cv)) continue;
+        const cplx<R> x = px[j], l = lx[j];
+        px[j] = py[j]; py[j] = x;
+        lx[j] = ly[j]; ly[j] = l;
+    }
+}
+
+template <typename R, int NP, int NA, bool CHK>
+__device__ __forceinline__ void run_pair(const AdjFOp<R> &os, const bool (&ok)[NP], const uint32_t (&i0)[NP],
+                                         cplx<R> (&px)[NP], cplx<R> (&py)[NP], cplx<R> (&lx)[NP],
+                                         cplx<R> (&ly)[NP], R &a0, R &a1) {
+    const uint32_t cm = os.cm, cv = os.cv;
+    const cplx<R> u0 = os.ui[0], u1 = os.ui[1], u2 = os.ui[2], u3 = os.ui[3];
+    cplx<R> g[4], h[4];
+    if (NA > 0) for (int e = 0; e < 4; ++e) g[e] = os.g0[e];
+    if (NA > 1) for (int e = 0; e < 4; ++e) h[e] = os.g1[e];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+        if (!ok[j] || (CHK && (i0[j] & cm) != cv)) continue;
+        const cplx<R> x = px[j], y = py[j], lxv = lx[j], lyv = ly[j];
+        if (NA > 0) a0 += pair_grad<R>(g, x, y, lxv, lyv);
+        if (NA > 1) a1 += pair_grad<R>(h, x, y, lxv, lyv);
+        px[j] = cmad2<R>(u0, x, u1, y); py[j] = cmad2<R>(u2, x, u3, y);
+        lx[j] = cmad2<R>(u0, lxv, u1, lyv); ly[j] = cmad2<R>(u2, lxv, u3, lyv);
+    }
+}
+
+// real U^dagger and real generators: Re<l|g x> = g Re(conj(l) x) term by term
+template <typename R, int NP, int NA, bool CHK>
+__device__ __forceinline__ void run_pair_real(const AdjFOp<R> &os, const bool (&ok)[NP], const uint32_t (&i0)[NP],
+                                              cplx<R> (&px)[NP], cplx<R> (&py)[NP], cplx<R> (&lx)[NP],
+                                              cplx<R> (&ly)[NP], R &a0, R &a1) {
+    const uint32_t cm = os.cm, cv = os.cv;
+    const R u0 = os.ui[0].x, u1 = os.ui[1].x, u2 = os.ui[2].x, u3 = os.ui[3].x;
+    R g[4] = {}, h[4] = {};
+    if (NA > 0) for (int e = 0; e < 4; ++e) g[e] = os.g0[e].x;
+    if (NA > 1) for (int e = 0; e < 4; ++e) h[e] = os.g1[e].x;
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+        if (!ok[j] || (CHK && (i0[j] & cm) != cv)) continue;
+        const cplx<R> x = px[j], y = py[j], lxv = lx[j], lyv = ly[j];
+        if (NA > 0) {
+            const R xx = rdot<R>(lxv, x), xy = rdot<R>(lxv, y), yx = rdot<R>(lyv, x), yy = rdot<R>(lyv, y);
+            a0 += g[0] * xx + g[1] * xy + g[2] * yx + g[3] * yy;
+            if (NA > 1) a1 += h[0] * xx + h[1] * xy + h[2] * yx + h[3] * yy;
+        }
+        px[j] = rmad2<R>(u0, x, u1, y); py[j] = rmad2<R>(u2, x, u3, y);
+        lx[j] = rmad2<R>(u0, lxv, u1, lyv); ly[j] = rmad2<R>(u2, lxv, u3, lyv);
+    }
+}
+
+template <typename R, int NA>
+__device__ __forceinline__ void diag_elem(bool one, cplx<R> d0, cplx<R> d1, cplx<R> g0, cplx<R> g3, cplx<R> h0,
+                                          cplx<R> h3, cplx<R> &x, cplx<R> &l, R &a0, R &a1) {
+    if (NA > 0) a0 += rdot<R>(l, cmul<R>(one ? g3 : g0, x));
+    if (NA > 1) a1 += rdot<R>(l, cmul<R>(one ? h3 : h0, x));
+    const cplx<R> d = one ? d1 : d0;
+    x = cmul<R>(d, x);
+    l = cmul<R>(d, l);
+}
+
+template <typename R, int NP, int NA, bool CHK>
+__device__ __forceinline__ void run_diag(const AdjFOp<R> &os, bool outer_one, uint32_t tb, const bool (&ok)[NP],
+                                         const uint32_t (&i0)[NP], cplx<R> (&px)[NP], cplx<R> (&py)[NP],
+                                         cplx<R> (&lx)[NP], cplx<R> (&ly)[NP], R &a0, R &a1) {
+    const uint32_t cm = os.cm, cv = os.cv;
+    const int tpos = os.tpos;
+    const bool tile_bit = os.mode == 2;
+    // a diagonal on the run's own bit: the pair's elements take d0 and d1
+    const bool on_run_bit = tile_bit && (1u << tpos) == tb;
+    const cplx<R> d0 = os.ui[0], d1 = os.ui[3];
+    cplx<R> g0{}, g3{}, h0{}, h3{};
+    if (NA > 0) { g0 = os.g0[0]; g3 = os.g0[3]; }
+    if (NA > 1) { h0 = os.g1[0]; h3 = os.g1[3]; }
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+        if (!ok[j]) continue;
+        const uint32_t e0 = i0[j], e1 = i0[j] | tb;
+        const bool one0 = tile_bit ? ((e0 >> tpos) & 1) : outer_one;
+        const bool one1 = one0 || on_run_bit;
+        if (!CHK || (e0 & cm) == cv) diag_elem<R, NA>(one0, d0, d1, g0, g3, h0, h3, px[j], lx[j], a0, a1);
+        if (!CHK || (e1 & cm) == cv) diag_elem<R, NA>(one1, d0, d1, g0, g3, h0, h3, py[j], ly[j], a0, a1);
+    }
+}
+
+template <typename R, int NP, bool CHK>
+__device__ __forceinline__ void step_on_pairs(const AdjFOp<R> &os, uint64_t base, uint32_t tb, const bool (&ok)[NP],
+                                              const uint32_t (&i0)[NP], cplx<R> (&px)[NP], cplx<R> (&py)[NP],
+                                              cplx<R> (&lx)[NP], cplx<R> (&ly)[NP], R &a0, R &a1) {
+    const int mode = os.mode, nang = os.nang;
+    if (mode == 1) {
+        run_exchange<R, NP, CHK>(os.cm, os.cv, ok, i0, px, py, lx, ly);
+    } else if (mode == 4) {
+        if (nang == 0) run_pair_real<R, NP, 0, CHK>(os, ok, i0, px, py, lx, ly, a0, a1);
+        else if (nang == 1) run_pair_real<R, NP, 1, CHK>(os, ok, i0, px, py, lx, ly, a0, a1);
+        else run_pair_real<R, NP, 2, CHK>(os, ok, i0, px, py, lx, ly, a0, a1);
+    } else if (mode == 0) {
+        if (nang == 0) run_pair<R, NP, 0, CHK>(os, ok, i0, px, py, lx, ly, a0, a1);
+        else if (nang == 1) run_pair<R, NP, 1, CHK>(os, ok, i0, px, py, lx, ly, a0, a1);
+        else run_pair<R, NP, 2, CHK>(os, ok, i0, px, py, lx, ly, a0, a1);
+    } else {
+        const bool outer_one = mode == 3 && ((base >> os.tpos) & 1);
+        if (nang == 0) run_diag<R, NP, 0, CHK>(os, outer_one, tb, ok, i0, px, py, lx, ly, a0, a1);
+        else if (nang == 1) run_diag<R, NP, 1, CHK>(os, outer_one, tb, ok, i0, px, py, lx, ly, a0, a1);
+        else run_diag<R, NP, 2, CHK>(os, outer_one, tb, ok, i0, px, py, lx, ly, a0, a1);
+    }
+}
+
+// pairs per thread: tiles of 2^12 (complex64) or 2^11 (complex128) amplitudes
+template <typename R>
+constexpr int adj_np() { return sizeof(R) == 4 ? 8 : 4; }
+
 template <typename R>
 __global__ void __launch_bounds__(AF_THREADS, 2) k_adj_pass(cplx<R> *__restrict__ psi, cplx<R> *__restrict__ lam,
                                                             const __grid_constant__ AdjFPass<R> P,
                                                             double *__restrict__ part) {
+    constexpr int NP = adj_np<R>();
     extern __shared__ __align__(16) unsigned char smraw[];
     const int K = P.K;
     const uint32_t T = 1u << K;
@@ -309,59 +442,48 @@ __global__ void __launch_bounds__(AF_THREADS, 2) k_adj_pass(cplx<R> *__restrict_
             sl[e] = lam[gi];
         }
         __syncthreads();
-        for (int k = 0; k < P.nops; ++k) {
-            const AdjFOp<R> &os = sops[k];
-            const uint64_t om = os.om, ov = os.ov;
-            if ((base & om) != ov) continue;            // the same for the whole tile
-            const int mode = os.mode, tpos = os.tpos, nang = os.nang;
-            const uint32_t cm = os.cm, cv = os.cv;
-            const cplx<R> u0 = os.ui[0], u1 = os.ui[1], u2 = os.ui[2], u3 = os.ui[3];
-            const cplx<R> a0g[4] = {os.g0[0], os.g0[1], os.g0[2], os.g0[3]};
-            const cplx<R> a1g[4] = {os.g1[0], os.g1[1], os.g1[2], os.g1[3]};
-            R a0 = R(0), a1 = R(0);
-            if (mode <= 1) {
-                const uint32_t tb = 1u << tpos;
-#pragma unroll 4
-                for (uint32_t p = tid; p < T / 2; p += AF_THREADS) {
-                    const uint32_t i0 = ((p >> tpos) << (tpos + 1)) | (p & (tb - 1));
-                    if ((i0 & cm) != cv) continue;
-                    const uint32_t i1 = i0 | tb;
-                    const cplx<R> px = sp[i0], py = sp[i1], lx = sl[i0], ly = sl[i1];
-                    if (nang > 0) {
-                        a0 += pair_grad<R>(a0g, px, py, lx, ly);
-                        if (nang > 1) a1 += pair_grad<R>(a1g, px, py, lx, ly);
-                    }
-                    if (mode == 1) {
-                        sp[i0] = py; sp[i1] = px; sl[i0] = ly; sl[i1] = lx;
-                    } else {
-                        sp[i0] = cmad2<R>(u0, px, u1, py); sp[i1] = cmad2<R>(u2, px, u3, py);
-                        sl[i0] = cmad2<R>(u0, lx, u1, ly); sl[i1] = cmad2<R>(u2, lx, u3, ly);
-                    }
-                }
-            } else {
-                const bool outer_one = mode == 3 && ((base >> tpos) & 1);
-#pragma unroll 4
-                for (uint32_t e = tid; e < T; e += AF_THREADS) {
-                    if ((e & cm) != cv) continue;
-                    const bool one = mode == 2 ? ((e >> tpos) & 1) : outer_one;
-                    const cplx<R> x = sp[e], l = sl[e];
-                    if (nang > 0) {
-                        a0 += rdot<R>(l, cmul<R>(one ? a0g[3] : a0g[0], x));
-                        if (nang > 1) a1 += rdot<R>(l, cmul<R>(one ? a1g[3] : a1g[0], x));
-                    }
-                    const cplx<R> d = one ? u3 : u0;
-                    sp[e] = cmul<R>(d, x);
-                    sl[e] = cmul<R>(d, l);
+        int k0 = 0;
+        for (int r = 0; r < P.nrun; ++r) {
+            const int t = P.run_bit[r], len = P.run_len[r];
+            const uint32_t tb = 1u << t;
+            // this thread's pairs (i0, i0 | tb) of the run's bit
+            uint32_t i0[NP];
+            bool ok[NP];
+            cplx<R> px[NP], py[NP], lx[NP], ly[NP];
+#pragma unroll
+            for (int j = 0; j < NP; ++j) {
+                const uint32_t p = tid + uint32_t(j) * AF_THREADS;
+                ok[j] = p < T / 2;
+                i0[j] = ((p >> t) << (t + 1)) | (p & (tb - 1));
+                if (ok[j]) {
+                    px[j] = sp[i0[j]]; py[j] = sp[i0[j] | tb];
+                    lx[j] = sl[i0[j]]; ly[j] = sl[i0[j] | tb];
                 }
             }
-            if (nang > 0) {
-                const double s0 = warp_sum_d<R>(a0);
-                if (lane == 0) sacc[os.acc * AF_WARPS + warp] += s0;
-                if (nang > 1) {
-                    const double s1 = warp_sum_d<R>(a1);
-                    if (lane == 0) sacc[(os.acc + 1) * AF_WARPS + warp] += s1;
+            for (int k = k0; k < k0 + len; ++k) {
+                const AdjFOp<R> &os = sops[k];
+                if ((base & os.om) != os.ov) continue;            // the same for the whole tile
+                const int nang = os.nang;
+                R a0 = R(0), a1 = R(0);
+                if (os.cm == 0) step_on_pairs<R, NP, false>(os, base, tb, ok, i0, px, py, lx, ly, a0, a1);
+                else step_on_pairs<R, NP, true>(os, base, tb, ok, i0, px, py, lx, ly, a0, a1);
+                if (nang > 0) {
+                    const double s0 = warp_sum_d<R>(a0);
+                    if (lane == 0) sacc[os.acc * AF_WARPS + warp] += s0;
+                    if (nang > 1) {
+                        const double s1 = warp_sum_d<R>(a1);
+                        if (lane == 0) sacc[(os.acc + 1) * AF_WARPS + warp] += s1;
+                    }
                 }
             }
+#pragma unroll
+            for (int j = 0; j < NP; ++j) {
+                if (ok[j]) {
+                    sp[i0[j]] = px[j]; sp[i0[j] | tb] = py[j];
+                    sl[i0[j]] = lx[j]; sl[i0[j] | tb] = ly[j];
+                }
+            }
+            k0 += len;
             __syncthreads();
         }
 #pragma unroll 4
@@ -394,12 +516,68 @@ struct Buf {
     ~Buf() { if (p) cudaFreeAsync(p, s); }
 };
 
-// at most ADJ_MAX_OPS steps per pass (the planner counts two budget units per op)
-constexpr int ADJ_MAX_OPS = 64;
-
 template <typename R>
 size_t adj_smem(int K, int nacc, int nops) {
     return (sizeof(cplx<R>) << (K + 1)) + sizeof(double) * AF_WARPS * size_t(nacc) + sizeof(AdjFOp<R>) * size_t(nops);
+}
+
+// true when the step's generators are real, as U^dagger is (mode 4)
+bool real_gens(const AdjStep &d) {
+    for (int e = 0; e < 4; ++e)
+        if (d.g0[2 * e + 1] != 0.0 || d.g1[2 * e + 1] != 0.0) return false;
+    return true;
+}
+
+// Orders a pass's steps (idx, in sweep order) into runs: the next step is the
+// first ready one (every earlier step it does not commute with already
+// placed) that is diagonal or targets the current run's bit; when none is,
+// the run ends and the first ready step opens the next.  Two steps commute
+// when every index bit they share is a control or the target of a diagonal
+// step for both (the test the pass planner uses), and moving a step past
+// steps it commutes with leaves every gradient term unchanged.  runs holds
+// (length, global target bit or -1 for a run of diagonal steps only).
+void schedule_runs(const std::vector<int> &idx, const std::vector<AdjStep> &steps, const std::vector<HostOp> &hops,
+                   std::vector<int> &order, std::vector<std::pair<int, int>> &runs) {
+    const size_t m = idx.size();
+    std::vector<uint64_t> sup(m), dg(m);
+    std::vector<char> diag(m);
+    for (size_t k = 0; k < m; ++k) {
+        const HostOp &o = hops[size_t(idx[k])];
+        diag[k] = steps[size_t(idx[k])].cls == AC_DIAG;
+        sup[k] = o.cmask | (uint64_t(1) << o.bit);
+        dg[k] = o.cmask | (diag[k] ? uint64_t(1) << o.bit : 0);
+    }
+    std::vector<std::vector<int>> succ(m);
+    std::vector<int> npred(m, 0);
+    for (size_t b = 0; b < m; ++b)
+        for (size_t a = 0; a < b; ++a)
+            if ((sup[a] & sup[b]) & ~(dg[a] & dg[b])) { succ[a].push_back(int(b)); ++npred[b]; }
+    std::set<int> ready;
+    for (size_t k = 0; k < m; ++k)
+        if (npred[k] == 0) ready.insert(int(k));
+    order.clear();
+    runs.clear();
+    int cur = -1, len = 0;
+    while (order.size() < m) {
+        int pick = -1;
+        for (int k : ready) {
+            const int b = hops[size_t(idx[size_t(k)])].bit;
+            if (diag[size_t(k)] || cur < 0 || b == cur) { pick = k; break; }
+        }
+        if (pick < 0) {
+            runs.push_back({len, cur});
+            cur = -1;
+            len = 0;
+            continue;
+        }
+        if (!diag[size_t(pick)] && cur < 0) cur = hops[size_t(idx[size_t(pick)])].bit;
+        order.push_back(idx[size_t(pick)]);
+        ++len;
+        ready.erase(pick);
+        for (int sidx : succ[size_t(pick)])
+            if (--npred[size_t(sidx)] == 0) ready.insert(sidx);
+    }
+    if (len > 0) runs.push_back({len, cur});
 }
 
 // The fused reverse sweep over steps[] (in forward order; run last to first).
@@ -436,8 +614,17 @@ cudaError_t fused_sweep(qs_state *s, const std::vector<AdjStep> &steps, const st
         P.tiles = uint64_t(1) << (n - K);
         for (int k = 0; k < K; ++k) P.tile_pos[k] = uint8_t(tp[k]);
         offs.push_back(flat.size());
+        std::vector<int> order;
+        std::vector<std::pair<int, int>> runs;
+        schedule_runs(gp.idx, steps, hops, order, runs);
+        if (runs.size() > size_t(ADJ_MAX_OPS)) return cudaErrorInvalidValue;
+        P.nrun = int(runs.size());
+        for (size_t r = 0; r < runs.size(); ++r) {
+            P.run_len[r] = uint8_t(runs[r].first);
+            P.run_bit[r] = uint8_t(runs[r].second < 0 ? K - 1 : local[runs[r].second]);
+        }
         int nacc = 0;
-        for (int j : gp.idx) {
+        for (int j : order) {
             const AdjStep &d = steps[size_t(j)];
             const HostOp &o = hops[size_t(j)];
             AdjFOp<R> f;
@@ -448,7 +635,7 @@ cudaError_t fused_sweep(qs_state *s, const std::vector<AdjStep> &steps, const st
                 else { f.mode = 3; f.tpos = b; }
             } else {
                 if (local[b] < 0) return cudaErrorInvalidValue;   // the planner keeps targets in the tile
-                f.mode = d.cls == AC_X ? 1 : 0;
+                f.mode = d.cls == AC_X ? 1 : d.cls == AC_REAL && real_gens(d) ? 4 : 0;
                 f.tpos = local[b];
             }
             for (int c = 0; c < n; ++c) {
