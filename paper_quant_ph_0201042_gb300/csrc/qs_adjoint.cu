@@ -405,6 +405,8 @@ __device__ __forceinline__ void step_on_pairs(const AdjFOp<R> &os, uint64_t base
 // pairs per thread: tiles of 2^12 (complex64) or 2^11 (complex128) amplitudes
 template <typename R>
 constexpr int adj_np() { return sizeof(R) == 4 ? 8 : 4; }
+template <typename R>
+constexpr int adj_full_k() { return sizeof(R) == 4 ? 12 : 11; }
 
 template <typename R>
 __global__ void __launch_bounds__(AF_THREADS, 2) k_adj_pass(cplx<R> *__restrict__ psi, cplx<R> *__restrict__ lam,
@@ -418,8 +420,17 @@ __global__ void __launch_bounds__(AF_THREADS, 2) k_adj_pass(cplx<R> *__restrict_
     cplx<R> *sl = sp + T;
     double *sacc = reinterpret_cast<double *>(sl + T);                        // nacc x AF_WARPS
     AdjFOp<R> *sops = reinterpret_cast<AdjFOp<R> *>(sacc + P.nacc * AF_WARPS);   // the pass's steps
+    // global offset of each value of the tile index's high K - 5 bits (the low
+    // five tile bits are index bits 0..4)
+    uint64_t *hoff = reinterpret_cast<uint64_t *>(sops + P.nops);
     const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
     for (int k = tid; k < P.nacc * AF_WARPS; k += AF_THREADS) sacc[k] = 0.0;
+    for (uint32_t h = tid; h < (T >> 5); h += AF_THREADS) {
+        uint64_t o = 0;
+        for (int k = 5; k < K; ++k)
+            if ((h >> (k - 5)) & 1) o |= uint64_t(1) << P.tile_pos[k];
+        hoff[h] = o;
+    }
     {
         const uint4 *src = reinterpret_cast<const uint4 *>(P.ops);
         uint4 *dst = reinterpret_cast<uint4 *>(sops);
@@ -435,9 +446,7 @@ __global__ void __launch_bounds__(AF_THREADS, 2) k_adj_pass(cplx<R> *__restrict_
         __syncthreads();
 #pragma unroll 4
         for (uint32_t e = tid; e < T; e += AF_THREADS) {
-            uint64_t gi = base;
-            for (int k = 0; k < K; ++k)
-                if ((e >> k) & 1) gi |= uint64_t(1) << P.tile_pos[k];
+            const uint64_t gi = base | hoff[e >> 5] | (e & 31u);
             sp[e] = psi[gi];
             sl[e] = lam[gi];
         }
@@ -488,9 +497,7 @@ __global__ void __launch_bounds__(AF_THREADS, 2) k_adj_pass(cplx<R> *__restrict_
         }
 #pragma unroll 4
         for (uint32_t e = tid; e < T; e += AF_THREADS) {
-            uint64_t gi = base;
-            for (int k = 0; k < K; ++k)
-                if ((e >> k) & 1) gi |= uint64_t(1) << P.tile_pos[k];
+            const uint64_t gi = base | hoff[e >> 5] | (e & 31u);
             psi[gi] = sp[e];
             lam[gi] = sl[e];
         }
@@ -518,7 +525,8 @@ struct Buf {
 
 template <typename R>
 size_t adj_smem(int K, int nacc, int nops) {
-    return (sizeof(cplx<R>) << (K + 1)) + sizeof(double) * AF_WARPS * size_t(nacc) + sizeof(AdjFOp<R>) * size_t(nops);
+    return (sizeof(cplx<R>) << (K + 1)) + sizeof(double) * AF_WARPS * size_t(nacc) + sizeof(AdjFOp<R>) * size_t(nops) +
+           (sizeof(uint64_t) << (K - 5));
 }
 
 // true when the step's generators are real, as U^dagger is (mode 4)
@@ -786,7 +794,7 @@ qs_status run_adjoint(qs_state *s, const std::vector<qs_gate> &gg, size_t n_para
     const int nslot = int(slot_param.size());
     // fused sweep: tiles of 2^K amplitudes (64 KiB per vector), one CTA per
     // tile at a time, as many CTAs as fit
-    const int Kf = std::min(n, sizeof(R) == 4 ? 12 : 11);
+    const int Kf = std::min(n, adj_full_k<R>());
     const bool fused = fuse && n >= 6;
     int nblk = RED_BLOCKS;
     if (fused) {
