@@ -269,15 +269,16 @@ struct AdjFPass {
     uint8_t tile_pos[16];
     uint8_t run_len[ADJ_MAX_OPS];
     uint8_t run_bit[ADJ_MAX_OPS];
+    uint8_t run_pre[ADJ_MAX_OPS];    // leading exchange steps of the run, applied at its load
 };
 
 // warp sum in the state's precision (the few FP64 units stay free for the
-// per-warp accumulators, which are double)
+// per-warp accumulators, which are double and updated by lane 0 alone)
 template <typename R>
-__device__ __forceinline__ double warp_sum_d(R v) {
+__device__ __forceinline__ R warp_sum(R v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return double(v);
+    return v;
 }
 
 template <typename R>
@@ -346,36 +347,55 @@ __device__ __forceinline__ void run_pair_real(const AdjFOp<R> &os, const bool (&
 }
 
 template <typename R, int NA>
-__device__ __forceinline__ void diag_elem(bool one, cplx<R> d0, cplx<R> d1, cplx<R> g0, cplx<R> g3, cplx<R> h0,
-                                          cplx<R> h3, cplx<R> &x, cplx<R> &l, R &a0, R &a1) {
-    if (NA > 0) a0 += rdot<R>(l, cmul<R>(one ? g3 : g0, x));
-    if (NA > 1) a1 += rdot<R>(l, cmul<R>(one ? h3 : h0, x));
-    const cplx<R> d = one ? d1 : d0;
+__device__ __forceinline__ void diag_elem(cplx<R> d, cplx<R> g, cplx<R> h, cplx<R> &x, cplx<R> &l, R &a0, R &a1) {
+    if (NA > 0) a0 += rdot<R>(l, cmul<R>(g, x));
+    if (NA > 1) a1 += rdot<R>(l, cmul<R>(h, x));
     x = cmul<R>(d, x);
     l = cmul<R>(d, l);
 }
 
-template <typename R, int NP, int NA, bool CHK>
+// DK: where the diagonal's bit lies.  0: the run's own bit (the pair's
+// elements take d0 and d1); 1: an outer bit (one entry for the whole tile);
+// 2: another tile bit (one entry per pair).
+template <typename R, int NP, int NA, bool CHK, int DK>
 __device__ __forceinline__ void run_diag(const AdjFOp<R> &os, bool outer_one, uint32_t tb, const bool (&ok)[NP],
                                          const uint32_t (&i0)[NP], cplx<R> (&px)[NP], cplx<R> (&py)[NP],
                                          cplx<R> (&lx)[NP], cplx<R> (&ly)[NP], R &a0, R &a1) {
     const uint32_t cm = os.cm, cv = os.cv;
     const int tpos = os.tpos;
-    const bool tile_bit = os.mode == 2;
-    // a diagonal on the run's own bit: the pair's elements take d0 and d1
-    const bool on_run_bit = tile_bit && (1u << tpos) == tb;
-    const cplx<R> d0 = os.ui[0], d1 = os.ui[3];
+    cplx<R> d0 = os.ui[0], d1 = os.ui[3];
     cplx<R> g0{}, g3{}, h0{}, h3{};
     if (NA > 0) { g0 = os.g0[0]; g3 = os.g0[3]; }
     if (NA > 1) { h0 = os.g1[0]; h3 = os.g1[3]; }
+    if (DK == 1 && outer_one) { d0 = d1; g0 = g3; h0 = h3; }
 #pragma unroll
     for (int j = 0; j < NP; ++j) {
         if (!ok[j]) continue;
         const uint32_t e0 = i0[j], e1 = i0[j] | tb;
-        const bool one0 = tile_bit ? ((e0 >> tpos) & 1) : outer_one;
-        const bool one1 = one0 || on_run_bit;
-        if (!CHK || (e0 & cm) == cv) diag_elem<R, NA>(one0, d0, d1, g0, g3, h0, h3, px[j], lx[j], a0, a1);
-        if (!CHK || (e1 & cm) == cv) diag_elem<R, NA>(one1, d0, d1, g0, g3, h0, h3, py[j], ly[j], a0, a1);
+        cplx<R> da = d0, db = d1, ga = g0, gb = g3, ha = h0, hb = h3;
+        if (DK == 1) { db = d0; gb = g0; hb = h0; }
+        if (DK == 2) {
+            const bool one = (e0 >> tpos) & 1;
+            da = db = one ? d1 : d0;
+            if (NA > 0) ga = gb = one ? g3 : g0;
+            if (NA > 1) ha = hb = one ? h3 : h0;
+        }
+        if (!CHK || (e0 & cm) == cv) diag_elem<R, NA>(da, ga, ha, px[j], lx[j], a0, a1);
+        if (!CHK || (e1 & cm) == cv) diag_elem<R, NA>(db, gb, hb, py[j], ly[j], a0, a1);
+    }
+}
+
+template <typename R, int NP, int NA, bool CHK>
+__device__ __forceinline__ void run_diag_any(const AdjFOp<R> &os, uint64_t base, uint32_t tb, const bool (&ok)[NP],
+                                             const uint32_t (&i0)[NP], cplx<R> (&px)[NP], cplx<R> (&py)[NP],
+                                             cplx<R> (&lx)[NP], cplx<R> (&ly)[NP], R &a0, R &a1) {
+    if (os.mode == 3) {
+        const bool outer_one = (base >> os.tpos) & 1;
+        run_diag<R, NP, NA, CHK, 1>(os, outer_one, tb, ok, i0, px, py, lx, ly, a0, a1);
+    } else if ((1u << os.tpos) == tb) {
+        run_diag<R, NP, NA, CHK, 0>(os, false, tb, ok, i0, px, py, lx, ly, a0, a1);
+    } else {
+        run_diag<R, NP, NA, CHK, 2>(os, false, tb, ok, i0, px, py, lx, ly, a0, a1);
     }
 }
 
@@ -395,10 +415,9 @@ __device__ __forceinline__ void step_on_pairs(const AdjFOp<R> &os, uint64_t base
         else if (nang == 1) run_pair<R, NP, 1, CHK>(os, ok, i0, px, py, lx, ly, a0, a1);
         else run_pair<R, NP, 2, CHK>(os, ok, i0, px, py, lx, ly, a0, a1);
     } else {
-        const bool outer_one = mode == 3 && ((base >> os.tpos) & 1);
-        if (nang == 0) run_diag<R, NP, 0, CHK>(os, outer_one, tb, ok, i0, px, py, lx, ly, a0, a1);
-        else if (nang == 1) run_diag<R, NP, 1, CHK>(os, outer_one, tb, ok, i0, px, py, lx, ly, a0, a1);
-        else run_diag<R, NP, 2, CHK>(os, outer_one, tb, ok, i0, px, py, lx, ly, a0, a1);
+        if (nang == 0) run_diag_any<R, NP, 0, CHK>(os, base, tb, ok, i0, px, py, lx, ly, a0, a1);
+        else if (nang == 1) run_diag_any<R, NP, 1, CHK>(os, base, tb, ok, i0, px, py, lx, ly, a0, a1);
+        else run_diag_any<R, NP, 2, CHK>(os, base, tb, ok, i0, px, py, lx, ly, a0, a1);
     }
 }
 
@@ -459,17 +478,33 @@ __global__ void __launch_bounds__(AF_THREADS, 2) k_adj_pass(cplx<R> *__restrict_
             uint32_t i0[NP];
             bool ok[NP];
             cplx<R> px[NP], py[NP], lx[NP], ly[NP];
+            // the run's leading exchange steps (C-NOT-like, on the run's bit)
+            // become the choice of which element of the pair loads as x
+            bool flip[NP];
 #pragma unroll
             for (int j = 0; j < NP; ++j) {
                 const uint32_t p = tid + uint32_t(j) * AF_THREADS;
                 ok[j] = p < T / 2;
                 i0[j] = ((p >> t) << (t + 1)) | (p & (tb - 1));
+                flip[j] = false;
+            }
+            const int pre = P.run_pre[r];
+            for (int k = k0; k < k0 + pre; ++k) {
+                const AdjFOp<R> &os = sops[k];
+                if ((base & os.om) != os.ov) continue;
+                const uint32_t cm = os.cm, cv = os.cv;
+#pragma unroll
+                for (int j = 0; j < NP; ++j) flip[j] ^= (i0[j] & cm) == cv;
+            }
+#pragma unroll
+            for (int j = 0; j < NP; ++j) {
                 if (ok[j]) {
-                    px[j] = sp[i0[j]]; py[j] = sp[i0[j] | tb];
-                    lx[j] = sl[i0[j]]; ly[j] = sl[i0[j] | tb];
+                    const uint32_t ia = flip[j] ? i0[j] | tb : i0[j], ib = ia ^ tb;
+                    px[j] = sp[ia]; py[j] = sp[ib];
+                    lx[j] = sl[ia]; ly[j] = sl[ib];
                 }
             }
-            for (int k = k0; k < k0 + len; ++k) {
+            for (int k = k0 + pre; k < k0 + len; ++k) {
                 const AdjFOp<R> &os = sops[k];
                 if ((base & os.om) != os.ov) continue;            // the same for the whole tile
                 const int nang = os.nang;
@@ -477,11 +512,11 @@ __global__ void __launch_bounds__(AF_THREADS, 2) k_adj_pass(cplx<R> *__restrict_
                 if (os.cm == 0) step_on_pairs<R, NP, false>(os, base, tb, ok, i0, px, py, lx, ly, a0, a1);
                 else step_on_pairs<R, NP, true>(os, base, tb, ok, i0, px, py, lx, ly, a0, a1);
                 if (nang > 0) {
-                    const double s0 = warp_sum_d<R>(a0);
-                    if (lane == 0) sacc[os.acc * AF_WARPS + warp] += s0;
+                    const R s0 = warp_sum<R>(a0);
+                    if (lane == 0) sacc[os.acc * AF_WARPS + warp] += double(s0);
                     if (nang > 1) {
-                        const double s1 = warp_sum_d<R>(a1);
-                        if (lane == 0) sacc[(os.acc + 1) * AF_WARPS + warp] += s1;
+                        const R s1 = warp_sum<R>(a1);
+                        if (lane == 0) sacc[(os.acc + 1) * AF_WARPS + warp] += double(s1);
                     }
                 }
             }
@@ -663,6 +698,11 @@ cudaError_t fused_sweep(qs_state *s, const std::vector<AdjStep> &steps, const st
                 f.g1[e] = cmat<R>(d.g1, e);
             }
             flat.push_back(f);
+        }
+        for (size_t r = 0, k = offs.back(); r < runs.size(); k += size_t(runs[r].first), ++r) {
+            int pre = 0;
+            while (pre < runs[r].first && flat[k + size_t(pre)].mode == 1) ++pre;
+            P.run_pre[r] = uint8_t(pre);
         }
         P.nops = int(gp.idx.size());
         P.nacc = nacc;
