@@ -421,6 +421,32 @@ __device__ __forceinline__ void step_on_pairs(const AdjFOp<R> &os, uint64_t base
     }
 }
 
+// Moves a tile of psi and lambda between HBM and shared memory (LOAD: in).
+// Element e of the tile is index base | hoff[e >> 5] | (e & 31); complex64
+// moves two neighbouring elements per 16-byte access.
+template <typename R, bool LOAD>
+__device__ __forceinline__ void tile_io(cplx<R> *__restrict__ psi, cplx<R> *__restrict__ lam, cplx<R> *sp, cplx<R> *sl,
+                                        uint64_t base, const uint64_t *hoff, uint32_t T, uint32_t tid) {
+    if constexpr (sizeof(R) == 4) {
+#pragma unroll 8
+        for (uint32_t q = tid; q < T / 2; q += AF_THREADS) {
+            const uint32_t e = 2 * q;
+            const uint64_t gi = base | hoff[e >> 5] | (e & 31u);
+            float4 *gp = reinterpret_cast<float4 *>(psi + gi), *gl = reinterpret_cast<float4 *>(lam + gi);
+            float4 *tp = reinterpret_cast<float4 *>(sp + e), *tl = reinterpret_cast<float4 *>(sl + e);
+            if (LOAD) { *tp = *gp; *tl = *gl; }
+            else { *gp = *tp; *gl = *tl; }
+        }
+    } else {
+#pragma unroll 8
+        for (uint32_t e = tid; e < T; e += AF_THREADS) {
+            const uint64_t gi = base | hoff[e >> 5] | (e & 31u);
+            if (LOAD) { sp[e] = psi[gi]; sl[e] = lam[gi]; }
+            else { psi[gi] = sp[e]; lam[gi] = sl[e]; }
+        }
+    }
+}
+
 // pairs per thread: tiles of 2^12 (complex64) or 2^11 (complex128) amplitudes
 template <typename R>
 constexpr int adj_np() { return sizeof(R) == 4 ? 8 : 4; }
@@ -463,12 +489,7 @@ __global__ void __launch_bounds__(AF_THREADS, 2) k_adj_pass(cplx<R> *__restrict_
             base = ((base & ~low) << 1) | (base & low);
         }
         __syncthreads();
-#pragma unroll 4
-        for (uint32_t e = tid; e < T; e += AF_THREADS) {
-            const uint64_t gi = base | hoff[e >> 5] | (e & 31u);
-            sp[e] = psi[gi];
-            sl[e] = lam[gi];
-        }
+        tile_io<R, true>(psi, lam, sp, sl, base, hoff, T, tid);
         __syncthreads();
         int k0 = 0;
         for (int r = 0; r < P.nrun; ++r) {
@@ -530,12 +551,7 @@ __global__ void __launch_bounds__(AF_THREADS, 2) k_adj_pass(cplx<R> *__restrict_
             k0 += len;
             __syncthreads();
         }
-#pragma unroll 4
-        for (uint32_t e = tid; e < T; e += AF_THREADS) {
-            const uint64_t gi = base | hoff[e >> 5] | (e & 31u);
-            psi[gi] = sp[e];
-            lam[gi] = sl[e];
-        }
+        tile_io<R, false>(psi, lam, sp, sl, base, hoff, T, tid);
     }
     __syncthreads();
     // one partial per generator slot and CTA
