@@ -253,6 +253,9 @@ struct alignas(16) AdjFOp {    // one reverse step of a pass, tile-local form
     int32_t nang;              // generators accumulated (0, 1, 2)
     int32_t acc;               // first accumulator of this pass used by the step
     int32_t slot0, slot1;      // global partial-sum slots of the generators
+    int32_t gk;                // one generator of a special form: 1 real antisymmetric [[0, -g], [g, 0]]
+                               // (mode 4), 2 imaginary diagonal diag(i a, i b) (modes 2, 3); else 0
+    int32_t pad_[3];
     cplx<R> ui[4];             // U^dagger
     cplx<R> g0[4], g1[4];      // generators dU U^dagger
 };
@@ -346,6 +349,29 @@ __device__ __forceinline__ void run_pair_real(const AdjFOp<R> &os, const bool (&
     }
 }
 
+// one real antisymmetric generator [[0, -g], [g, 0]]:
+// Re<l|G|psi> = g (Re(conj(ly) x) - Re(conj(lx) y))
+template <typename R, int NP, bool CHK>
+__device__ __forceinline__ void run_pair_real_as(const AdjFOp<R> &os, const bool (&ok)[NP], const uint32_t (&i0)[NP],
+                                                 cplx<R> (&px)[NP], cplx<R> (&py)[NP], cplx<R> (&lx)[NP],
+                                                 cplx<R> (&ly)[NP], R &a0) {
+    const uint32_t cm = os.cm, cv = os.cv;
+    const R u0 = os.ui[0].x, u1 = os.ui[1].x, u2 = os.ui[2].x, u3 = os.ui[3].x;
+    R t = R(0);
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+        if (!ok[j] || (CHK && (i0[j] & cm) != cv)) continue;
+        const cplx<R> x = px[j], y = py[j], lxv = lx[j], lyv = ly[j];
+        t = fma(lyv.x, x.x, t);
+        t = fma(lyv.y, x.y, t);
+        t = fma(-lxv.x, y.x, t);
+        t = fma(-lxv.y, y.y, t);
+        px[j] = rmad2<R>(u0, x, u1, y); py[j] = rmad2<R>(u2, x, u3, y);
+        lx[j] = rmad2<R>(u0, lxv, u1, lyv); ly[j] = rmad2<R>(u2, lxv, u3, lyv);
+    }
+    a0 += os.g0[2].x * t;
+}
+
 template <typename R, int NA>
 __device__ __forceinline__ void diag_elem(cplx<R> d, cplx<R> g, cplx<R> h, cplx<R> &x, cplx<R> &l, R &a0, R &a1) {
     if (NA > 0) a0 += rdot<R>(l, cmul<R>(g, x));
@@ -354,10 +380,18 @@ __device__ __forceinline__ void diag_elem(cplx<R> d, cplx<R> g, cplx<R> h, cplx<
     l = cmul<R>(d, l);
 }
 
+// one imaginary diagonal generator entry i g: Re<l|i g x> = g (l.y x.x - l.x x.y)
+template <typename R>
+__device__ __forceinline__ void diag_elem_im(cplx<R> d, R g, cplx<R> &x, cplx<R> &l, R &a0) {
+    a0 = fma(g, fma(l.y, x.x, -l.x * x.y), a0);
+    x = cmul<R>(d, x);
+    l = cmul<R>(d, l);
+}
+
 // DK: where the diagonal's bit lies.  0: the run's own bit (the pair's
 // elements take d0 and d1); 1: an outer bit (one entry for the whole tile);
 // 2: another tile bit (one entry per pair).
-template <typename R, int NP, int NA, bool CHK, int DK>
+template <typename R, int NP, int NA, bool CHK, int DK, bool IM>
 __device__ __forceinline__ void run_diag(const AdjFOp<R> &os, bool outer_one, uint32_t tb, const bool (&ok)[NP],
                                          const uint32_t (&i0)[NP], cplx<R> (&px)[NP], cplx<R> (&py)[NP],
                                          cplx<R> (&lx)[NP], cplx<R> (&ly)[NP], R &a0, R &a1) {
@@ -380,22 +414,27 @@ __device__ __forceinline__ void run_diag(const AdjFOp<R> &os, bool outer_one, ui
             if (NA > 0) ga = gb = one ? g3 : g0;
             if (NA > 1) ha = hb = one ? h3 : h0;
         }
-        if (!CHK || (e0 & cm) == cv) diag_elem<R, NA>(da, ga, ha, px[j], lx[j], a0, a1);
-        if (!CHK || (e1 & cm) == cv) diag_elem<R, NA>(db, gb, hb, py[j], ly[j], a0, a1);
+        if (IM) {
+            if (!CHK || (e0 & cm) == cv) diag_elem_im<R>(da, ga.y, px[j], lx[j], a0);
+            if (!CHK || (e1 & cm) == cv) diag_elem_im<R>(db, gb.y, py[j], ly[j], a0);
+        } else {
+            if (!CHK || (e0 & cm) == cv) diag_elem<R, NA>(da, ga, ha, px[j], lx[j], a0, a1);
+            if (!CHK || (e1 & cm) == cv) diag_elem<R, NA>(db, gb, hb, py[j], ly[j], a0, a1);
+        }
     }
 }
 
-template <typename R, int NP, int NA, bool CHK>
+template <typename R, int NP, int NA, bool CHK, bool IM>
 __device__ __forceinline__ void run_diag_any(const AdjFOp<R> &os, uint64_t base, uint32_t tb, const bool (&ok)[NP],
                                              const uint32_t (&i0)[NP], cplx<R> (&px)[NP], cplx<R> (&py)[NP],
                                              cplx<R> (&lx)[NP], cplx<R> (&ly)[NP], R &a0, R &a1) {
     if (os.mode == 3) {
         const bool outer_one = (base >> os.tpos) & 1;
-        run_diag<R, NP, NA, CHK, 1>(os, outer_one, tb, ok, i0, px, py, lx, ly, a0, a1);
+        run_diag<R, NP, NA, CHK, 1, IM>(os, outer_one, tb, ok, i0, px, py, lx, ly, a0, a1);
     } else if ((1u << os.tpos) == tb) {
-        run_diag<R, NP, NA, CHK, 0>(os, false, tb, ok, i0, px, py, lx, ly, a0, a1);
+        run_diag<R, NP, NA, CHK, 0, IM>(os, false, tb, ok, i0, px, py, lx, ly, a0, a1);
     } else {
-        run_diag<R, NP, NA, CHK, 2>(os, false, tb, ok, i0, px, py, lx, ly, a0, a1);
+        run_diag<R, NP, NA, CHK, 2, IM>(os, false, tb, ok, i0, px, py, lx, ly, a0, a1);
     }
 }
 
@@ -407,7 +446,8 @@ __device__ __forceinline__ void step_on_pairs(const AdjFOp<R> &os, uint64_t base
     if (mode == 1) {
         run_exchange<R, NP, CHK>(os.cm, os.cv, ok, i0, px, py, lx, ly);
     } else if (mode == 4) {
-        if (nang == 0) run_pair_real<R, NP, 0, CHK>(os, ok, i0, px, py, lx, ly, a0, a1);
+        if (os.gk == 1) run_pair_real_as<R, NP, CHK>(os, ok, i0, px, py, lx, ly, a0);
+        else if (nang == 0) run_pair_real<R, NP, 0, CHK>(os, ok, i0, px, py, lx, ly, a0, a1);
         else if (nang == 1) run_pair_real<R, NP, 1, CHK>(os, ok, i0, px, py, lx, ly, a0, a1);
         else run_pair_real<R, NP, 2, CHK>(os, ok, i0, px, py, lx, ly, a0, a1);
     } else if (mode == 0) {
@@ -415,11 +455,34 @@ __device__ __forceinline__ void step_on_pairs(const AdjFOp<R> &os, uint64_t base
         else if (nang == 1) run_pair<R, NP, 1, CHK>(os, ok, i0, px, py, lx, ly, a0, a1);
         else run_pair<R, NP, 2, CHK>(os, ok, i0, px, py, lx, ly, a0, a1);
     } else {
-        if (nang == 0) run_diag_any<R, NP, 0, CHK>(os, base, tb, ok, i0, px, py, lx, ly, a0, a1);
-        else if (nang == 1) run_diag_any<R, NP, 1, CHK>(os, base, tb, ok, i0, px, py, lx, ly, a0, a1);
-        else run_diag_any<R, NP, 2, CHK>(os, base, tb, ok, i0, px, py, lx, ly, a0, a1);
+        if (os.gk == 2) run_diag_any<R, NP, 1, CHK, true>(os, base, tb, ok, i0, px, py, lx, ly, a0, a1);
+        else if (nang == 0) run_diag_any<R, NP, 0, CHK, false>(os, base, tb, ok, i0, px, py, lx, ly, a0, a1);
+        else if (nang == 1) run_diag_any<R, NP, 1, CHK, false>(os, base, tb, ok, i0, px, py, lx, ly, a0, a1);
+        else run_diag_any<R, NP, 2, CHK, false>(os, base, tb, ok, i0, px, py, lx, ly, a0, a1);
     }
 }
+
+// Per-warp gradient accumulators over the tiles a CTA visits.  complex64:
+// a compensated (Kahan) float sum, so the FP32 pipe does the work and the
+// error does not grow with the number of tiles; complex128: double.
+template <typename R>
+struct Acc { double s; };
+template <>
+struct Acc<float> { float s, c; };
+
+template <typename R>
+__device__ __forceinline__ void acc_add(Acc<R> &a, R v) { a.s += double(v); }
+template <>
+__device__ __forceinline__ void acc_add<float>(Acc<float> &a, float v) {
+    const float y = v - a.c;
+    const float t = a.s + y;
+    a.c = (t - a.s) - y;
+    a.s = t;
+}
+template <typename R>
+__device__ __forceinline__ double acc_value(const Acc<R> &a) { return a.s; }
+template <>
+__device__ __forceinline__ double acc_value<float>(const Acc<float> &a) { return double(a.s) - double(a.c); }
 
 // Moves a tile of psi and lambda between HBM and shared memory (LOAD: in).
 // Element e of the tile is index base | hoff[e >> 5] | (e & 31); complex64
@@ -463,13 +526,13 @@ __global__ void __launch_bounds__(AF_THREADS, 2) k_adj_pass(cplx<R> *__restrict_
     const uint32_t T = 1u << K;
     cplx<R> *sp = reinterpret_cast<cplx<R> *>(smraw);
     cplx<R> *sl = sp + T;
-    double *sacc = reinterpret_cast<double *>(sl + T);                        // nacc x AF_WARPS
+    Acc<R> *sacc = reinterpret_cast<Acc<R> *>(sl + T);                        // nacc x AF_WARPS
     AdjFOp<R> *sops = reinterpret_cast<AdjFOp<R> *>(sacc + P.nacc * AF_WARPS);   // the pass's steps
     // global offset of each value of the tile index's high K - 5 bits (the low
     // five tile bits are index bits 0..4)
     uint64_t *hoff = reinterpret_cast<uint64_t *>(sops + P.nops);
     const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
-    for (int k = tid; k < P.nacc * AF_WARPS; k += AF_THREADS) sacc[k] = 0.0;
+    for (int k = tid; k < P.nacc * AF_WARPS; k += AF_THREADS) sacc[k] = Acc<R>{};
     for (uint32_t h = tid; h < (T >> 5); h += AF_THREADS) {
         uint64_t o = 0;
         for (int k = 5; k < K; ++k)
@@ -534,10 +597,10 @@ __global__ void __launch_bounds__(AF_THREADS, 2) k_adj_pass(cplx<R> *__restrict_
                 else step_on_pairs<R, NP, true>(os, base, tb, ok, i0, px, py, lx, ly, a0, a1);
                 if (nang > 0) {
                     const R s0 = warp_sum<R>(a0);
-                    if (lane == 0) sacc[os.acc * AF_WARPS + warp] += double(s0);
+                    if (lane == 0) acc_add<R>(sacc[os.acc * AF_WARPS + warp], s0);
                     if (nang > 1) {
                         const R s1 = warp_sum<R>(a1);
-                        if (lane == 0) sacc[(os.acc + 1) * AF_WARPS + warp] += double(s1);
+                        if (lane == 0) acc_add<R>(sacc[(os.acc + 1) * AF_WARPS + warp], s1);
                     }
                 }
             }
@@ -559,7 +622,7 @@ __global__ void __launch_bounds__(AF_THREADS, 2) k_adj_pass(cplx<R> *__restrict_
         const AdjFOp<R> &o = sops[k];
         for (int a = 0; a < o.nang; ++a) {
             if (tid < 32) {
-                double v = lane < AF_WARPS ? sacc[(o.acc + a) * AF_WARPS + lane] : 0.0;
+                double v = lane < AF_WARPS ? acc_value<R>(sacc[(o.acc + a) * AF_WARPS + lane]) : 0.0;
 #pragma unroll
                 for (int q = 16; q > 0; q >>= 1) v += __shfl_xor_sync(0xffffffffu, v, q);
                 if (lane == 0) part[uint64_t(a == 0 ? o.slot0 : o.slot1) * gridDim.x + blockIdx.x] = v;
@@ -576,7 +639,7 @@ struct Buf {
 
 template <typename R>
 size_t adj_smem(int K, int nacc, int nops) {
-    return (sizeof(cplx<R>) << (K + 1)) + sizeof(double) * AF_WARPS * size_t(nacc) + sizeof(AdjFOp<R>) * size_t(nops) +
+    return (sizeof(cplx<R>) << (K + 1)) + sizeof(Acc<R>) * AF_WARPS * size_t(nacc) + sizeof(AdjFOp<R>) * size_t(nops) +
            (sizeof(uint64_t) << (K - 5));
 }
 
@@ -704,6 +767,9 @@ cudaError_t fused_sweep(qs_state *s, const std::vector<AdjStep> &steps, const st
                 else { f.om |= uint64_t(1) << c; if (one) f.ov |= uint64_t(1) << c; }
             }
             f.nang = d.nang;
+            // generator entries (re, im) at 2e, 2e + 1 for e = 0..3
+            if (f.mode == 4 && d.nang == 1 && d.g0[0] == 0.0 && d.g0[6] == 0.0 && d.g0[2] == -d.g0[4]) f.gk = 1;
+            if ((f.mode == 2 || f.mode == 3) && d.nang == 1 && d.g0[0] == 0.0 && d.g0[6] == 0.0) f.gk = 2;
             f.acc = nacc;
             f.slot0 = d.slot0;
             f.slot1 = d.slot1;
