@@ -127,6 +127,49 @@ def test_fused_sweep_every_gate_kind(dtype, n):
         assert np.max(np.abs(grad - want)) < GTOL[dtype] * 4, (fuse, np.max(np.abs(grad - want)))
 
 
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_fused_sweep_runs_of_one_target(dtype):
+    # steps grouped on one target bit: several C-NOTs in a row on it with
+    # controls on lane, warp and outer bits (they fold into the run's load),
+    # diagonals controlled by the run's own bit, diagonals on outer bits and
+    # on other tile bits, real and complex rotations, all against the
+    # oracle's parameter-shift rule
+    n = 15
+    r = W.rng(1515)
+    gates, k = W.hadamard_layer(n), 0
+    for t in (0, 4, 6, 9, 13):
+        others = [x for x in range(n) if x != t]
+        block = []
+        for _ in range(3):
+            c = int(r.choice(others))
+            block.append(W.Gate("X", t, controls={c: int(r.integers(2))}))
+        for kind in ("RZ", "UP1", "RY", "UR", "URP1"):
+            na = 2 if kind == "URP1" else 1
+            ctr = {int(r.choice(others)): int(r.integers(2))} if r.random() < 0.5 else {}
+            block.append(W.Gate(kind, t, controls=ctr, angles=(0.0,) * na, param=k))
+            k += na
+        d = int(r.choice(others))
+        block.append(W.Gate("RZ", d, controls={t: 1}, angles=(0.0,), param=k))      # controlled by the run's bit
+        k += 1
+        block.append(W.Gate("UP1", int(r.choice(others)), angles=(0.0,), param=k))  # another bit, uncontrolled
+        k += 1
+        gates += block
+        gates.append(W.Gate("X", (t + 1) % n, controls={t: 1}))
+    params = r.uniform(-math.pi, math.pi, size=k)
+    # <Z_t> for each block's target: together they reach most parameters
+    seen = np.zeros(k)
+    for t in (0, 4, 6, 9, 13):
+        pauli = "".join("Z" if q == t else "I" for q in range(n))
+        want = oracle.gradient(n, gates, params, pauli=pauli, method="shift")
+        want_val = oracle.cost(n, gates, params, pauli=pauli)
+        seen = np.maximum(seen, np.abs(want))
+        for fuse in (True, False):
+            val, grad = qs.adjoint_grad(qs.State(n, dtype), gates, params, pauli=pauli, fuse=fuse)
+            assert abs(val - want_val) < GTOL[dtype], (t, fuse)
+            assert np.max(np.abs(grad - want)) < GTOL[dtype] * 4, (t, fuse, np.max(np.abs(grad - want)))
+    assert np.sum(seen > 1e-3) > 25
+
+
 def test_autograd_function_matches():
     n = 8
     gates, params = W.ansatz_circuit(n, 4, seed=12)
