@@ -474,19 +474,26 @@ def main():
         e2e_step()
         if dist:
             dist.barrier()
+        k = max(1, min(args.steps, 5))
+        esampler = ClockSampler(local)
+        esampler.start()
+        step_ms = []
         t0 = time.perf_counter()
-        k = max(1, min(args.steps, 3))
         for _ in range(k):
-            e2e_step()
+            ts = time.perf_counter()
+            e2e_step()          # ends with the synchronous copy-out
+            step_ms.append((time.perf_counter() - ts) * 1e3)
         torch.cuda.synchronize()
         dt = max_over_ranks((time.perf_counter() - t0) / k, dist)
+        eclocks = esampler.stop()
         # the device-to-host copy alone (what the host link adds to the step)
         t1 = time.perf_counter()
         qs.check(qs.lib().qs_copy_out(state.handle, hbuf.ctypes.data_as(ctypes.c_void_p), hbuf.nbytes))
         tc = time.perf_counter() - t1
         line["e2e"] = {"value": world * upd / dt, "unit": "amp-updates/s",
                        "h2d_bytes_per_step": ctypes.sizeof(garr), "d2h_bytes_per_step": hbuf.nbytes,
-                       "ms_per_step": dt * 1e3, "steps": k,
+                       "ms_per_step": dt * 1e3, "steps": k, "step_ms": [round(v, 2) for v in step_ms],
+                       "clocks": eclocks,
                        "d2h_copy_ms": tc * 1e3, "d2h_gbs": hbuf.nbytes / tc / 1e9,
                        "host_buffer_pinned": bool(host.is_pinned())}
         del host
