@@ -12,10 +12,12 @@
 // pair is handled by one thread that reads the four amplitudes before writing
 // any (the in-place rule of Sec. 2.2.1).
 //
-// Sums: each block adds its pairs (complex64: single-precision per thread,
-// then double across threads; complex128: double throughout) and writes one
-// partial per angle; fixed-order reductions then give one sum per angle and
-// one per parameter.
+// Sums: each block adds its pairs and writes one partial per angle;
+// fixed-order reductions then give one sum per angle and one per parameter.
+// complex128 sums in double throughout.  complex64: single precision per
+// thread and across the warp; the per-step sweep then adds across threads in
+// double, the fused sweep keeps a compensated (Kahan) float accumulator per
+// warp over the tiles it visits and adds the warps in double.
 //
 // Fused sweep (default): the reverse steps are grouped into tile passes by
 // the fused planner's pass formation (steps whose targets lie in a tile of
@@ -24,7 +26,9 @@
 // dU_j U_j^dagger).  A CTA loads the tile of psi and of lambda into shared
 // memory once, runs the pass's steps on it (gradient partial, then the
 // uncompute) and writes both tiles back: one HBM round trip of the two vectors
-// per pass instead of per step.
+// per pass instead of per step.  Within the tile the steps run in runs that
+// share one target bit (diagonal steps join any run): each thread keeps its
+// pairs of both vectors in registers for a whole run.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -275,8 +279,7 @@ struct AdjFPass {
     uint8_t run_pre[ADJ_MAX_OPS];    // leading exchange steps of the run, applied at its load
 };
 
-// warp sum in the state's precision (the few FP64 units stay free for the
-// per-warp accumulators, which are double and updated by lane 0 alone)
+// warp sum in the state's precision; lane 0 adds it to the warp's accumulator
 template <typename R>
 __device__ __forceinline__ R warp_sum(R v) {
 #pragma unroll
