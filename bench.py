@@ -297,6 +297,30 @@ def secondary(args, torch, qs, state64):
                            "seconds": dt, "trajectories_per_s": len(met) / dt,
                            "amp_updates_per_s": tupd / dt,
                            "histogram_0_1_10bins": hist.tolist(), "mean_metric": float(met.mean())}
+
+    # Grover search, n = 24, floor(pi/4 sqrt(2^24)) = 3216 iterations, as one
+    # plan; success probability against sin^2((2j+1) theta), sin theta = 2^-12
+    gn = 24
+    gk = W.basis_index(24, gn)
+    git = W.grover_iterations(gn)
+    ggates = W.grover_circuit(gn, gk, git)
+    want = math.sin((2 * git + 1) * math.asin(2.0 ** (-gn / 2))) ** 2
+    gro = {"workload": "Grover n=24, %d iterations (%d gates: 2 H layers and 2 one-amplitude phase flips "
+                       "per iteration)" % (git, len(ggates))}
+    for dt_name, B in (("c64", 8), ("c128", 16)):
+        gs = qs.State(gn, dt_name)
+        gp = qs.Plan(gn, dt_name, ggates)
+        run = lambda: (gs.init_basis(0), gp.execute(gs))
+        run()
+        ms = _time(torch, run)
+        p_succ = gs.prob(gk)
+        gro[dt_name] = {"ms": ms, "gates_per_s": len(ggates) / (ms / 1e3), "passes": gp.launches,
+                        "hbm_gbs": gp.launches * 2.0 * (B << gn) / (ms / 1e3) / 1e9,
+                        "success_probability": p_succ, "closed_form": want, "error": abs(p_succ - want)}
+        gro[dt_name]["frac_of_measured_hbm"] = gro[dt_name]["hbm_gbs"] / measured_peaks()[0]
+        gs.close()
+        del gp
+    out["grover_n24"] = gro
     return out
 
 
