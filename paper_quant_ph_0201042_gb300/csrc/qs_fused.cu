@@ -505,6 +505,35 @@ __device__ __forceinline__ void s_diag(float2 (&v)[NA], float2 d0, float2 d1, ui
     }
 }
 
+// Diagonal on register slot T with one entry exactly 1: only the amplitudes
+// whose physical bit T equals BIT change (the caller turns the logical side
+// into the physical one with bit T of xm).
+template <int T, int NA, int BIT>
+__device__ __forceinline__ void s_diag_half(float2 (&v)[NA], float2 d, uint32_t xm, int rm, int rv) {
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+        if (((j >> T) & 1) != BIT) continue;
+        if (lpred(j, xm, rm, rv)) v[j] = cmul<float>(d, v[j]);
+    }
+}
+
+// d0 == 1 exactly: the logical-one side changes; d1 == 1: the logical-zero
+// side; otherwise both (s_diag).
+template <int T, int NA>
+__device__ __forceinline__ void s_diag_any(float2 (&v)[NA], float2 d0, float2 d1, uint32_t xm, int rm, int rv) {
+    const bool id0 = d0.x == 1.f && d0.y == 0.f, id1 = d1.x == 1.f && d1.y == 0.f;
+    const uint32_t xt = (xm >> T) & 1u;
+    if (id0) {
+        if (xt) s_diag_half<T, NA, 0>(v, d1, xm, rm, rv);
+        else s_diag_half<T, NA, 1>(v, d1, xm, rm, rv);
+    } else if (id1) {
+        if (xt) s_diag_half<T, NA, 1>(v, d0, xm, rm, rv);
+        else s_diag_half<T, NA, 0>(v, d0, xm, rm, rv);
+    } else {
+        s_diag<T, NA>(v, d0, d1, xm, rm, rv);
+    }
+}
+
 template <int T, int NA>
 __device__ __forceinline__ void s_reg_op(float2 (&v)[NA], int cls, uint32_t &xm, bool ok, int rm, int rv, bool lanectl,
                                          const Mat4<float> &m) {
@@ -714,14 +743,15 @@ __global__ void __launch_bounds__(32 << QS_WB64, QS_FUSED_MINBLOCKS) k_fused_c64
                 if (!ok) continue;
                 const float2 d0 = mt.u00, d1 = mt.u01;
                 if (tsel == 0) {
-                    if (tpos == 0) s_diag<0, NA>(v, d0, d1, xm, rm, rv2);
-                    else if (tpos == 1) s_diag<1, NA>(v, d0, d1, xm, rm, rv2);
-                    else if (tpos == 2) s_diag<2, NA>(v, d0, d1, xm, rm, rv2);
-                    else if (tpos == 3) s_diag<3, NA>(v, d0, d1, xm, rm, rv2);
-                    else s_diag<(RB64 > 4 ? 4 : 0), NA>(v, d0, d1, xm, rm, rv2);
+                    if (tpos == 0) s_diag_any<0, NA>(v, d0, d1, xm, rm, rv2);
+                    else if (tpos == 1) s_diag_any<1, NA>(v, d0, d1, xm, rm, rv2);
+                    else if (tpos == 2) s_diag_any<2, NA>(v, d0, d1, xm, rm, rv2);
+                    else if (tpos == 3) s_diag_any<3, NA>(v, d0, d1, xm, rm, rv2);
+                    else s_diag_any<(RB64 > 4 ? 4 : 0), NA>(v, d0, d1, xm, rm, rv2);
                 } else {
                     const uint64_t word = tsel == 1 ? uint64_t(tl) : base;
                     const float2 d = ((word >> tpos) & 1) ? d1 : d0;
+                    if (d.x == 1.f && d.y == 0.f) continue;   // this thread's entry is exactly 1
 #pragma unroll
                     for (int j = 0; j < NA; ++j)
                         if (lpred(j, xm, rm, rv2)) v[j] = cmul<float>(d, v[j]);
