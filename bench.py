@@ -454,9 +454,9 @@ def main():
     t_alu = flops_step / (alu_peak * 1e12)
     main = alu_view if t_alu > t_hbm else hbm_view
     # DRAM traffic of one fused-pass launch from one ncu capture of this
-    # kernel at n = 26 (1014.2 MB read + write per launch), scaled to n by the
+    # kernel at n = 26 (1013.5 MB read + write per launch), scaled to n by the
     # amplitudes processed; only valid for the complex64 fused kernel
-    traffic = 1014.2e6 * (1 << (n - 26)) if (args.dtype == "c64" and not args.no_fuse) else None
+    traffic = 1013.5e6 * (1 << (n - 26)) if (args.dtype == "c64" and not args.no_fuse) else None
     roof = {"bound": "alu" if t_alu > t_hbm else "hbm", "achieved": main["achieved"], "peak": main["peak"],
             "unit": main["unit"], "frac": main["frac"], "traffic": traffic, "traffic_unit": "bytes per launch",
             "kernel": ("k_fused_c64" if args.dtype == "c64" else "k_fused<double,4>") if not args.no_fuse else "k_pair",
