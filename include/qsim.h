@@ -398,6 +398,21 @@ qs_status qs_adjoint_grad(qs_state *s, const qs_gate *g, size_t m, const double 
 qs_status qs_adjoint_grad_ex(qs_state *s, const qs_gate *g, size_t m, const double *params, size_t n_params,
                              const qs_observable *obs, double *value, double *grad, const qs_exec_opts *opts);
 
+/* Host-side plan of the fused reverse sweep that qs_adjoint_grad would run for
+ * this circuit on an n-qubit state of dtype dt.  It needs no GPU and uses the
+ * gates' own angles (theta).  Writes text into buf (NUL-terminated, truncated
+ * to len bytes); *needed (may be NULL) receives the full length + 1.  Lines:
+ *   step <j> cls=<gen|real|diag|x> bit=<index bit> cmask=<hex> cval=<hex> u=<8 numbers>
+ *     one per reverse step in forward order (a SWAP gives three C-NOT steps);
+ *     u is the step's forward matrix, (re, im) row-major
+ *   pass <p> tile=<index bits of the tile, ascending>
+ *   run bit=<index bit, or -1 for diagonal steps only> pre=<k> steps=<j,...>
+ *     the pass's runs in sweep order; the first k steps of a run are exchanges
+ * No pass lines for n < 6 (the per-step sweep runs there).
+ * Errors: QS_ERANGE for n out of range, QS_EINVAL for a bad dtype or NULL
+ * gates with m > 0, QS_EUNSUPPORTED for a gate the adjoint cannot take. */
+qs_status qs_adjoint_describe(int n, qs_dtype dt, const qs_gate *g, size_t m, char *buf, size_t len, size_t *needed);
+
 /* --------------------------------------------------------------------- */
 /* Host copies (checkpoint / restore)                                      */
 /* --------------------------------------------------------------------- */

@@ -126,6 +126,8 @@ _SIGS = {
     "qs_adjoint_grad_ex": [ctypes.c_void_p, ctypes.POINTER(QsGate), ctypes.c_size_t, ctypes.POINTER(ctypes.c_double),
                            ctypes.c_size_t, ctypes.POINTER(QsObservable), ctypes.POINTER(ctypes.c_double),
                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(QsExecOpts)],
+    "qs_adjoint_describe": [ctypes.c_int, ctypes.c_int, ctypes.POINTER(QsGate), ctypes.c_size_t, ctypes.c_char_p,
+                            ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)],
     "qs_copy_out": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t],
     "qs_copy_in": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t],
 }
@@ -433,6 +435,17 @@ def batch_groups(batch) -> list:
             g["target"] = batch.marked[k]
         out.append(g)
     return out
+
+
+def adjoint_describe(n: int, dtype: str, gates: Sequence) -> str:
+    """The fused reverse sweep's host-side plan for these gates (qs_adjoint_describe):
+    step lines, then per tile pass its runs of steps.  Needs no GPU."""
+    arr = gates_to_abi(gates)
+    need = ctypes.c_size_t()
+    check(lib().qs_adjoint_describe(n, DTYPES[dtype], arr, len(gates), None, 0, ctypes.byref(need)))
+    buf = ctypes.create_string_buffer(need.value)
+    check(lib().qs_adjoint_describe(n, DTYPES[dtype], arr, len(gates), buf, need.value, None))
+    return buf.value.decode()
 
 
 def adjoint_grad(work: "State", gates: Sequence, params, pauli: Optional[str] = None,

@@ -33,6 +33,8 @@
 #include <cmath>
 #include <cstring>
 #include <set>
+#include <string>
+#include <cstdio>
 #include <vector>
 
 #include "qs_internal.cuh"
@@ -705,13 +707,23 @@ void schedule_runs(const std::vector<int> &idx, const std::vector<AdjStep> &step
     if (len > 0) runs.push_back({len, cur});
 }
 
-// The fused reverse sweep over steps[] (in forward order; run last to first).
-template <typename R>
-cudaError_t fused_sweep(qs_state *s, const std::vector<AdjStep> &steps, const std::vector<HostOp> &hops,
-                        cplx<R> *psi, cplx<R> *lp, double *part, int grid, int K) {
-    const int n = s->n;
-    cudaStream_t st = s->stream;
-    // reverse steps as planner ops (SWAP already split into C-NOTs by the caller)
+// One tile pass of the fused reverse sweep, planned on the host: the tile's
+// index bits (ascending), the pass's steps in sweep order, its runs (length,
+// global target bit or -1 for diagonal steps only) and each run's leading
+// exchange steps.
+struct SweepPass {
+    std::vector<int> tile;
+    std::vector<int> order;
+    std::vector<std::pair<int, int>> runs;
+    std::vector<int> pre;
+};
+
+// Plans the fused reverse sweep over steps[] (in forward order; run last to
+// first) for tiles of 2^K amplitudes.  False if a pass's step targets a bit
+// outside its tile (the pass planner never does this).
+bool plan_sweep(int n, int K, const std::vector<AdjStep> &steps, const std::vector<HostOp> &hops,
+                std::vector<SweepPass> &out) {
+    // reverse steps as planner ops (SWAP already split into C-NOTs)
     std::vector<HostOp> rev;
     for (size_t j = steps.size(); j-- > 0;) {
         HostOp o = hops[j];
@@ -721,35 +733,57 @@ cudaError_t fused_sweep(qs_state *s, const std::vector<AdjStep> &steps, const st
         else o.cls = GC_GEN;
         rev.push_back(o);
     }
-    const int H = K - 5;
-    std::vector<PassGroup> groups = group_passes(n, H, 2 * ADJ_MAX_OPS, rev);
+    out.clear();
+    for (const PassGroup &gp : group_passes(n, K - 5, 2 * ADJ_MAX_OPS, rev)) {
+        SweepPass sp;
+        sp.tile = {0, 1, 2, 3, 4};
+        sp.tile.insert(sp.tile.end(), gp.high.begin(), gp.high.end());
+        std::sort(sp.tile.begin(), sp.tile.end());
+        schedule_runs(gp.idx, steps, hops, sp.order, sp.runs);
+        for (int j : sp.order)
+            if (steps[size_t(j)].cls != AC_DIAG &&
+                std::find(sp.tile.begin(), sp.tile.end(), hops[size_t(j)].bit) == sp.tile.end())
+                return false;
+        for (size_t r = 0, k = 0; r < sp.runs.size(); k += size_t(sp.runs[r].first), ++r) {
+            int pre = 0;
+            while (pre < sp.runs[r].first && steps[size_t(sp.order[k + size_t(pre)])].cls == AC_X) ++pre;
+            sp.pre.push_back(pre);
+        }
+        out.push_back(std::move(sp));
+    }
+    return true;
+}
+
+// The fused reverse sweep over steps[] (in forward order; run last to first).
+template <typename R>
+cudaError_t fused_sweep(qs_state *s, const std::vector<AdjStep> &steps, const std::vector<HostOp> &hops,
+                        cplx<R> *psi, cplx<R> *lp, double *part, int grid, int K) {
+    const int n = s->n;
+    cudaStream_t st = s->stream;
+    std::vector<SweepPass> plan;
+    if (!plan_sweep(n, K, steps, hops, plan)) return cudaErrorInvalidValue;
     std::vector<AdjFOp<R>> flat;
     std::vector<AdjFPass<R>> passes;
     std::vector<size_t> offs;
-    for (const PassGroup &gp : groups) {
-        std::vector<int> tp = {0, 1, 2, 3, 4};
-        tp.insert(tp.end(), gp.high.begin(), gp.high.end());
-        std::sort(tp.begin(), tp.end());
+    for (const SweepPass &sp : plan) {
         int local[64];
         for (int b = 0; b < 64; ++b) local[b] = -1;
-        for (int k = 0; k < K; ++k) local[tp[k]] = k;
+        for (int k = 0; k < K; ++k) local[sp.tile[size_t(k)]] = k;
         AdjFPass<R> P;
         std::memset(&P, 0, sizeof(P));
         P.K = K;
         P.tiles = uint64_t(1) << (n - K);
-        for (int k = 0; k < K; ++k) P.tile_pos[k] = uint8_t(tp[k]);
+        for (int k = 0; k < K; ++k) P.tile_pos[k] = uint8_t(sp.tile[size_t(k)]);
         offs.push_back(flat.size());
-        std::vector<int> order;
-        std::vector<std::pair<int, int>> runs;
-        schedule_runs(gp.idx, steps, hops, order, runs);
-        if (runs.size() > size_t(ADJ_MAX_OPS)) return cudaErrorInvalidValue;
-        P.nrun = int(runs.size());
-        for (size_t r = 0; r < runs.size(); ++r) {
-            P.run_len[r] = uint8_t(runs[r].first);
-            P.run_bit[r] = uint8_t(runs[r].second < 0 ? K - 1 : local[runs[r].second]);
+        if (sp.runs.size() > size_t(ADJ_MAX_OPS)) return cudaErrorInvalidValue;
+        P.nrun = int(sp.runs.size());
+        for (size_t r = 0; r < sp.runs.size(); ++r) {
+            P.run_len[r] = uint8_t(sp.runs[r].first);
+            P.run_bit[r] = uint8_t(sp.runs[r].second < 0 ? K - 1 : local[sp.runs[r].second]);
+            P.run_pre[r] = uint8_t(sp.pre[r]);
         }
         int nacc = 0;
-        for (int j : order) {
+        for (int j : sp.order) {
             const AdjStep &d = steps[size_t(j)];
             const HostOp &o = hops[size_t(j)];
             AdjFOp<R> f;
@@ -759,7 +793,6 @@ cudaError_t fused_sweep(qs_state *s, const std::vector<AdjStep> &steps, const st
                 if (local[b] >= 0) { f.mode = 2; f.tpos = local[b]; }
                 else { f.mode = 3; f.tpos = b; }
             } else {
-                if (local[b] < 0) return cudaErrorInvalidValue;   // the planner keeps targets in the tile
                 f.mode = d.cls == AC_X ? 1 : d.cls == AC_REAL && real_gens(d) ? 4 : 0;
                 f.tpos = local[b];
             }
@@ -784,12 +817,7 @@ cudaError_t fused_sweep(qs_state *s, const std::vector<AdjStep> &steps, const st
             }
             flat.push_back(f);
         }
-        for (size_t r = 0, k = offs.back(); r < runs.size(); k += size_t(runs[r].first), ++r) {
-            int pre = 0;
-            while (pre < runs[r].first && flat[k + size_t(pre)].mode == 1) ++pre;
-            P.run_pre[r] = uint8_t(pre);
-        }
-        P.nops = int(gp.idx.size());
+        P.nops = int(sp.order.size());
         P.nacc = nacc;
         passes.push_back(P);
     }
@@ -808,6 +836,75 @@ cudaError_t fused_sweep(qs_state *s, const std::vector<AdjStep> &steps, const st
     }
     cudaFreeAsync(dops, st);
     return e;
+}
+
+// The circuit's reverse steps in forward order: one per synthesised gate, a
+// SWAP as three C-NOTs; each differentiated angle gets a partial-sum slot,
+// slot_param lists (parameter, slot) in gate order.
+qs_status build_steps(int n, const std::vector<qs_gate> &gg, size_t n_params, std::vector<AdjStep> &steps,
+                      std::vector<HostOp> &hops, std::vector<std::pair<int, int>> &slot_param) {
+    qs_status rc = QS_OK;
+    for (size_t jg = 0; jg < gg.size(); ++jg) {
+        HostOp og;
+        rc = synthesize(n, gg[jg], og);
+        if (rc != QS_OK) return rc;
+        std::vector<HostOp> parts;
+        if (og.cls == GC_SWAP) {
+            HostOp x = og;
+            x.cls = GC_X;
+            x.kind = QS_GATE_X;
+            for (int k = 0; k < 8; ++k) x.u[k] = 0.0;
+            x.u[2] = 1.0; x.u[4] = 1.0;
+            HostOp c1 = x, c2 = x;
+            c1.bit = og.bit; c1.cmask = uint64_t(1) << og.bit2; c1.cval = uint64_t(1) << og.bit2;
+            c2.bit = og.bit2; c2.cmask = og.cmask | (uint64_t(1) << og.bit); c2.cval = og.cval | (uint64_t(1) << og.bit);
+            parts = {c1, c2, c1};
+        } else {
+            parts = {og};
+        }
+        for (const HostOp &o : parts) {
+            const size_t j = steps.size();
+            steps.emplace_back();
+            hops.push_back(o);
+            AdjStep &d = steps[j];
+            std::memset(&d, 0, sizeof(d));
+            std::vector<int> pos;
+            for (int b = 0; b < 64; ++b)
+                if ((o.cmask >> b) & 1) pos.push_back(b);
+            d.cval = o.cval;
+            d.tbit = uint64_t(1) << o.bit;
+            if (o.cls == GC_SWAP) {
+                d.cls = AC_SWAP;
+                d.tbit2 = uint64_t(1) << o.bit2;
+                pos.push_back(o.bit);
+                pos.push_back(o.bit2);
+            } else {
+                pos.push_back(o.bit);
+                dagger(o.u, d.ui);
+                d.cls = o.cls == GC_X ? AC_X
+                      : (o.cls == GC_DIAG || o.cls == GC_PHASE || o.cls == GC_ID) ? AC_DIAG
+                      : o.cls == GC_REAL ? AC_REAL : AC_GEN;
+            }
+            std::sort(pos.begin(), pos.end());
+            d.nfixed = int(pos.size());
+            for (size_t k = 0; k < pos.size(); ++k) d.pos[k] = uint8_t(pos[k]);
+            if (gg[jg].param >= 0) {
+                const int na = kind_angles(gg[jg].kind);
+                if (na == 0) return fail(QS_EUNSUPPORTED, "adjoint: a parameter on a gate kind without angles");
+                for (int a = 0; a < na; ++a) {
+                    const int pidx = gg[jg].param + a;
+                    if (pidx >= int(n_params)) return fail(QS_EINVAL, "adjoint: parameter index beyond n_params");
+                    double *g = a == 0 ? d.g0 : d.g1;
+                    generator(gg[jg].kind, a, gg[jg].theta[0], gg[jg].theta[1], g);
+                    const int slot = int(slot_param.size());
+                    (a == 0 ? d.slot0 : d.slot1) = slot;
+                    slot_param.push_back({pidx, slot});
+                }
+                d.nang = na;
+            }
+        }
+    }
+    return QS_OK;
 }
 
 template <typename R>
@@ -856,66 +953,8 @@ qs_status run_adjoint(qs_state *s, const std::vector<qs_gate> &gg, size_t n_para
     std::vector<AdjStep> steps;
     std::vector<HostOp> hops;
     std::vector<std::pair<int, int>> slot_param;   // (param, slot)
-    for (size_t jg = 0; jg < gg.size(); ++jg) {
-        HostOp og;
-        rc = synthesize(n, gg[jg], og);
-        if (rc != QS_OK) return rc;
-        std::vector<HostOp> parts;
-        if (og.cls == GC_SWAP) {
-            HostOp x = og;
-            x.cls = GC_X;
-            x.kind = QS_GATE_X;
-            for (int k = 0; k < 8; ++k) x.u[k] = 0.0;
-            x.u[2] = 1.0; x.u[4] = 1.0;
-            HostOp c1 = x, c2 = x;
-            c1.bit = og.bit; c1.cmask = uint64_t(1) << og.bit2; c1.cval = uint64_t(1) << og.bit2;
-            c2.bit = og.bit2; c2.cmask = og.cmask | (uint64_t(1) << og.bit); c2.cval = og.cval | (uint64_t(1) << og.bit);
-            parts = {c1, c2, c1};
-        } else {
-            parts = {og};
-        }
-        for (const HostOp &o : parts) {
-        const size_t j = steps.size();
-        steps.emplace_back();
-        hops.push_back(o);
-        AdjStep &d = steps[j];
-        std::memset(&d, 0, sizeof(d));
-        std::vector<int> pos;
-        for (int b = 0; b < 64; ++b)
-            if ((o.cmask >> b) & 1) pos.push_back(b);
-        d.cval = o.cval;
-        d.tbit = uint64_t(1) << o.bit;
-        if (o.cls == GC_SWAP) {
-            d.cls = AC_SWAP;
-            d.tbit2 = uint64_t(1) << o.bit2;
-            pos.push_back(o.bit);
-            pos.push_back(o.bit2);
-        } else {
-            pos.push_back(o.bit);
-            dagger(o.u, d.ui);
-            d.cls = o.cls == GC_X ? AC_X
-                  : (o.cls == GC_DIAG || o.cls == GC_PHASE || o.cls == GC_ID) ? AC_DIAG
-                  : o.cls == GC_REAL ? AC_REAL : AC_GEN;
-        }
-        std::sort(pos.begin(), pos.end());
-        d.nfixed = int(pos.size());
-        for (size_t k = 0; k < pos.size(); ++k) d.pos[k] = uint8_t(pos[k]);
-        if (gg[jg].param >= 0) {
-            const int na = kind_angles(gg[jg].kind);
-            if (na == 0) return fail(QS_EUNSUPPORTED, "adjoint: a parameter on a gate kind without angles");
-            for (int a = 0; a < na; ++a) {
-                const int pidx = gg[jg].param + a;
-                if (pidx >= int(n_params)) return fail(QS_EINVAL, "adjoint: parameter index beyond n_params");
-                double *g = a == 0 ? d.g0 : d.g1;
-                generator(gg[jg].kind, a, gg[jg].theta[0], gg[jg].theta[1], g);
-                const int slot = int(slot_param.size());
-                (a == 0 ? d.slot0 : d.slot1) = slot;
-                slot_param.push_back({pidx, slot});
-            }
-            d.nang = na;
-        }
-        }
-    }
+    rc = build_steps(n, gg, n_params, steps, hops, slot_param);
+    if (rc != QS_OK) return rc;
     const int nslot = int(slot_param.size());
     // fused sweep: tiles of 2^K amplitudes (64 KiB per vector), one CTA per
     // tile at a time, as many CTAs as fit
@@ -1023,4 +1062,57 @@ extern "C" qs_status qs_adjoint_grad_ex(qs_state *s, const qs_gate *g, size_t m,
     }
     return s->dt == QS_C64 ? run_adjoint<float>(s, gg, n_params, *obs, value, grad, fuse)
                            : run_adjoint<double>(s, gg, n_params, *obs, value, grad, fuse);
+}
+
+extern "C" qs_status qs_adjoint_describe(int n, qs_dtype dt, const qs_gate *g, size_t m, char *buf, size_t len,
+                                         size_t *needed) {
+    if (n < 1 || n > QS_MAX_QUBITS) return fail(QS_ERANGE, "n out of range");
+    if (dt != QS_C64 && dt != QS_C128) return fail(QS_EINVAL, "bad dtype");
+    if (m > 0 && !g) return fail(QS_EINVAL, "NULL argument");
+    std::vector<qs_gate> gg(g, g + m);
+    size_t n_params = 0;
+    for (const qs_gate &x : gg)
+        if (x.param >= 0) n_params = std::max(n_params, size_t(x.param) + size_t(std::max(kind_angles(x.kind), 1)));
+    std::vector<AdjStep> steps;
+    std::vector<HostOp> hops;
+    std::vector<std::pair<int, int>> slot_param;
+    qs_status rc = build_steps(n, gg, n_params, steps, hops, slot_param);
+    if (rc != QS_OK) return rc;
+    std::string out;
+    char line[640];
+    for (size_t j = 0; j < steps.size(); ++j) {
+        const HostOp &o = hops[j];
+        const int c = steps[j].cls;
+        const char *cls = c == AC_DIAG ? "diag" : c == AC_X ? "x" : c == AC_REAL ? "real" : "gen";
+        std::snprintf(line, sizeof(line),
+                      "step %zu cls=%s bit=%d cmask=%llx cval=%llx u=%.17g,%.17g,%.17g,%.17g,%.17g,%.17g,%.17g,%.17g\n", j,
+                      cls, int(o.bit), (unsigned long long)o.cmask, (unsigned long long)o.cval, o.u[0], o.u[1], o.u[2],
+                      o.u[3], o.u[4], o.u[5], o.u[6], o.u[7]);
+        out += line;
+    }
+    if (n >= 6) {
+        const int K = std::min(n, dt == QS_C64 ? adj_full_k<float>() : adj_full_k<double>());
+        std::vector<SweepPass> plan;
+        if (!plan_sweep(n, K, steps, hops, plan)) return fail(QS_EUNSUPPORTED, "adjoint plan: a target outside its tile");
+        for (size_t p = 0; p < plan.size(); ++p) {
+            out += "pass " + std::to_string(p) + " tile=";
+            for (size_t k = 0; k < plan[p].tile.size(); ++k) out += (k ? "," : "") + std::to_string(plan[p].tile[k]);
+            out += "\n";
+            size_t k = 0;
+            for (size_t r = 0; r < plan[p].runs.size(); ++r) {
+                out += "run bit=" + std::to_string(plan[p].runs[r].second) + " pre=" + std::to_string(plan[p].pre[r]) +
+                       " steps=";
+                for (int i = 0; i < plan[p].runs[r].first; ++i, ++k)
+                    out += (i ? "," : "") + std::to_string(plan[p].order[k]);
+                out += "\n";
+            }
+        }
+    }
+    if (needed) *needed = out.size() + 1;
+    if (buf && len) {
+        const size_t k = std::min(len - 1, out.size());
+        std::memcpy(buf, out.data(), k);
+        buf[k] = 0;
+    }
+    return QS_OK;
 }
