@@ -181,9 +181,13 @@ qs_status qs_plan_info(const qs_plan *p, int64_t *n_launches, int64_t *n_gates);
 
 qs_status qs_plan_free(qs_plan *p);
 
-/* Writes a human-readable description of the plan (one line per pass: tile
- * bits, op counts by kind, transposes) into buf (NUL-terminated, truncated to
- * len bytes).  *needed (may be NULL) receives the full length + 1. */
+/* Writes a human-readable description of the plan into buf (NUL-terminated,
+ * truncated to len bytes); *needed (may be NULL) receives the full length + 1.
+ * Fused plans: one line per pass (tile bits, op counts by kind, transposes),
+ * each followed by "  order=<i,...>", the pass's ops in execution order as
+ * indices into the planned op list; then one line per planned op (a SWAP
+ * appears as three C-NOTs):
+ *   op <i> bit=<index bit> cmask=<hex> cval=<hex> u=<8 numbers, (re, im) row-major> */
 qs_status qs_plan_describe(const qs_plan *p, char *buf, size_t len, size_t *needed);
 
 /* Per-launch timing of plan executions, for roofline measurement.  While

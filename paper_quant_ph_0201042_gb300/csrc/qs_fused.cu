@@ -840,6 +840,8 @@ struct Plan {
     bool temp = false;                       // stream-ordered table (one-shot plan)
     cudaStream_t free_stream = nullptr;
     int64_t n_gates = 0;
+    std::vector<HostOp> ex;                  // fused mode: the ops planned (SWAPs as C-NOTs); step = index
+    std::vector<std::vector<int>> order;     // fused mode: each pass's ops (indices into ex) in execution order
     int RB = 0;
     int grid = 0;                            // persistent grid size
     // per-launch timing (qs_plan_set_timing)
@@ -938,7 +940,8 @@ std::vector<HostOp> schedule_pass(const std::vector<HostOp> &ops, const std::map
 
 template <typename R>
 qs_status resolve_pass(int n, int RB, int WB, const PlannedPass &pp, PassDesc<R> &D,
-                       std::vector<FOp<R>> &ops_out, std::vector<TrajOpMeta> *metas = nullptr) {
+                       std::vector<FOp<R>> &ops_out, std::vector<TrajOpMeta> *metas = nullptr,
+                       std::vector<int> *order = nullptr) {
     const int H = RB + WB;
     std::memset(&D, 0, sizeof(D));
     D.K = LB + H;
@@ -954,6 +957,10 @@ qs_status resolve_pass(int n, int RB, int WB, const PlannedPass &pp, PassDesc<R>
     // trajectory mode keeps program order (its per-step Pauli frames follow it)
     const std::vector<HostOp> sched = metas ? pp.ops : schedule_pass(pp.ops, hidx, RB, H);
     const std::vector<HostOp> &ops = sched;
+    if (order) {
+        order->clear();
+        for (const HostOp &o : ops) order->push_back(o.step);
+    }
 
     // register-slot demand sequence: high index needed as a register bit by op k
     const size_t m = ops.size();
@@ -1180,17 +1187,20 @@ qs_status build_fused(Plan *P, const std::vector<HostOp> &ops, int max_ops,
     const int H = RB + WB;
     std::vector<HostOp> ex;
     expand_swaps(ops, ex);
+    for (size_t i = 0; i < ex.size(); ++i) ex[i].step = int32_t(i);
     std::vector<PlannedPass> passes = form_passes(n, H, max_ops, ex);
     out.resize(passes.size());
     tables.resize(passes.size());
+    P->order.assign(passes.size(), {});
     size_t total = 0;
     for (size_t k = 0; k < passes.size(); ++k) {
-        qs_status st = resolve_pass<R>(n, RB, WB, passes[k], out[k], tables[k]);
+        qs_status st = resolve_pass<R>(n, RB, WB, passes[k], out[k], tables[k], nullptr, &P->order[k]);
         if (st != QS_OK) return st;
         out[k].tiles = uint64_t(1) << (n - out[k].K);
         total += tables[k].size();
     }
     (void)total;
+    P->ex = std::move(ex);
     return QS_OK;
 }
 
@@ -1480,7 +1490,7 @@ qs_status plan_timing(Plan *p, double *ms, int64_t *launches) {
 namespace {
 template <typename R>
 void describe_passes(const std::vector<PassDesc<R>> &passes, const std::vector<std::vector<FOp<R>>> &tables,
-                     std::string &out) {
+                     const std::vector<std::vector<int>> &order, std::string &out) {
     for (size_t k = 0; k < passes.size(); ++k) {
         const PassDesc<R> &D = passes[k];
         // register ops: general (uncontrolled / register-controlled), Hadamard
@@ -1502,6 +1512,11 @@ void describe_passes(const std::vector<PassDesc<R>> &passes, const std::vector<s
                       "lane(gen=%d x=%d) diag=%d xpose=%d bits=[%s]\n",
                       k, D.K, D.WB, rg, rgc, rhb, rxd, rx, lg, lx, diag, xp, bits.c_str());
         out += line;
+        if (k < order.size()) {
+            out += "  order=";
+            for (size_t i = 0; i < order[k].size(); ++i) out += (i ? "," : "") + std::to_string(order[k][i]);
+            out += "\n";
+        }
     }
 }
 }  // namespace
@@ -1513,8 +1528,18 @@ std::string plan_describe(const Plan *p) {
                   p->dt == QS_C64 ? "c64" : "c128", (long long)p->n_gates, int(p->fused));
     out += head;
     if (!p->fused) return out;
-    if (p->dt == QS_C64) describe_passes<float>(p->pf, p->of, out);
-    else describe_passes<double>(p->pd, p->od, out);
+    if (p->dt == QS_C64) describe_passes<float>(p->pf, p->of, p->order, out);
+    else describe_passes<double>(p->pd, p->od, p->order, out);
+    // the planned ops (forward matrices, (re, im) row-major)
+    char line[640];
+    for (size_t i = 0; i < p->ex.size(); ++i) {
+        const HostOp &o = p->ex[i];
+        std::snprintf(line, sizeof(line),
+                      "op %zu bit=%d cmask=%llx cval=%llx u=%.17g,%.17g,%.17g,%.17g,%.17g,%.17g,%.17g,%.17g\n", i,
+                      int(o.bit), (unsigned long long)o.cmask, (unsigned long long)o.cval, o.u[0], o.u[1], o.u[2],
+                      o.u[3], o.u[4], o.u[5], o.u[6], o.u[7]);
+        out += line;
+    }
     return out;
 }
 
