@@ -426,6 +426,18 @@ qs_status qs_adjoint_describe(int n, qs_dtype dt, const qs_gate *g, size_t m, ch
 qs_status qs_copy_out(qs_state *s, void *host, size_t bytes);
 qs_status qs_copy_in(qs_state *s, const void *host, size_t bytes);
 
+/* Enqueues the copy of the whole state to host memory on the state's stream
+ * and returns without waiting: the host buffer holds the state once qs_sync(s)
+ * (or a synchronisation of that stream) returns, and must stay valid until
+ * then.  With page-locked (pinned) host memory the copy overlaps work on other
+ * streams; pageable memory makes it synchronous.  bytes as for qs_copy_out
+ * (QS_ERANGE otherwise); QS_EINVAL for NULL arguments. */
+qs_status qs_copy_out_async(qs_state *s, void *host, size_t bytes);
+
+/* Waits for all work enqueued on the state's stream; QS_ECUDA with the
+ * message of an asynchronous failure. */
+qs_status qs_sync(qs_state *s);
+
 /* Thread-local message describing the last failure of this thread. */
 const char *qs_last_error(void);
 

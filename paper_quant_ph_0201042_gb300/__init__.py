@@ -129,6 +129,8 @@ _SIGS = {
     "qs_adjoint_describe": [ctypes.c_int, ctypes.c_int, ctypes.POINTER(QsGate), ctypes.c_size_t, ctypes.c_char_p,
                             ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)],
     "qs_copy_out": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t],
+    "qs_copy_out_async": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t],
+    "qs_sync": [ctypes.c_void_p],
     "qs_copy_in": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t],
 }
 

@@ -418,6 +418,19 @@ qs_status qs_copy_out(qs_state *s, void *host, size_t bytes) {
     return e == cudaSuccess ? QS_OK : cuda_fail(e, "copy_out");
 }
 
+qs_status qs_copy_out_async(qs_state *s, void *host, size_t bytes) {
+    if (!s || !host) return fail(QS_EINVAL, "NULL argument");
+    if (bytes != (amp_size(s->dt) << s->n)) return fail(QS_ERANGE, "byte count does not match the state");
+    const cudaError_t e = cudaMemcpyAsync(host, s->d, bytes, cudaMemcpyDeviceToHost, s->stream);
+    return e == cudaSuccess ? QS_OK : cuda_fail(e, "copy_out_async");
+}
+
+qs_status qs_sync(qs_state *s) {
+    if (!s) return fail(QS_EINVAL, "state is NULL");
+    const cudaError_t e = cudaStreamSynchronize(s->stream);
+    return e == cudaSuccess ? QS_OK : cuda_fail(e, "sync");
+}
+
 qs_status qs_copy_in(qs_state *s, const void *host, size_t bytes) {
     if (!s || !host) return fail(QS_EINVAL, "NULL argument");
     if (bytes != (amp_size(s->dt) << s->n)) return fail(QS_ERANGE, "byte count does not match the state");
