@@ -263,6 +263,9 @@ def e2e_pipelined(torch, qs, state, n, dtype, garr, n_gates, opts, k, dist, loca
         return {"ms_per_step": dt * 1e3, "steps": k, "pipelined": True, "states": 2, "streams": 2,
                 "clocks": clocks, "host_buffers_pinned": all(bool(h.is_pinned()) for h in hosts)}
     finally:
+        # both streams idle before the second state goes and the first moves back
+        L.qs_sync(other.handle)
+        L.qs_sync(state.handle)
         qs.check(L.qs_set_stream(state.handle, ctypes.c_void_p(old_stream.cuda_stream)))
         other.close()
 
