@@ -75,6 +75,31 @@ def test_argument_errors_without_gpu(libpath):
     assert L.qs_plan_create(4, qs.QS_C64, bad, 1, None, ctypes.byref(p)) == 1
 
 
+def test_new_entry_points_validate_without_gpu(libpath):
+    L = qs.lib()
+    buf = ctypes.create_string_buffer(16)
+    assert L.qs_copy_out_async(None, buf, 16) == 1                  # QS_EINVAL
+    assert L.qs_sync(None) == 1
+    need = ctypes.c_size_t()
+    g = qs.gates_to_abi([W.Gate("H", 0)])
+    assert L.qs_adjoint_describe(0, qs.QS_C64, g, 1, None, 0, ctypes.byref(need)) == 2     # QS_ERANGE
+    assert L.qs_adjoint_describe(41, qs.QS_C64, g, 1, None, 0, ctypes.byref(need)) == 2
+    assert L.qs_adjoint_describe(4, 9, g, 1, None, 0, ctypes.byref(need)) == 1             # bad dtype
+    assert L.qs_adjoint_describe(4, qs.QS_C64, None, 1, None, 0, ctypes.byref(need)) == 1
+    bad = qs.gates_to_abi([W.Gate("H", 4)])                                                 # target out of range
+    assert L.qs_adjoint_describe(4, qs.QS_C64, bad, 1, None, 0, ctypes.byref(need)) != 0
+    # a parameter on a gate kind without angles
+    bad = qs.gates_to_abi([W.Gate("H", 1, param=0)])
+    assert L.qs_adjoint_describe(4, qs.QS_C64, bad, 1, None, 0, ctypes.byref(need)) == 6   # QS_EUNSUPPORTED
+    # an empty circuit describes itself as nothing, a truncated buffer stays NUL-terminated
+    assert L.qs_adjoint_describe(8, qs.QS_C64, None, 0, None, 0, ctypes.byref(need)) == 0 and need.value == 1
+    text = qs.adjoint_describe(8, "c64", W.ansatz_circuit(8, 1, seed=2)[0])
+    small = ctypes.create_string_buffer(10)
+    assert L.qs_adjoint_describe(8, qs.QS_C64, qs.gates_to_abi(W.ansatz_circuit(8, 1, seed=2)[0]), 23, small, 10,
+                                 None) == 0
+    assert small.value.decode() == text[:9]
+
+
 def test_plans_build_without_gpu(libpath):
     # planning is host-only: a fused plan of the 30-qubit random circuit
     gates = W.random_circuit(30, 2, seed=1)
