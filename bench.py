@@ -582,6 +582,10 @@ def main():
         except (RuntimeError, MemoryError) as exc:
             pipe = None
             line["e2e"]["pipelined_unavailable"] = str(exc).splitlines()[0][:200] if str(exc) else type(exc).__name__
+        # hand the pinned host buffers back to the system (torch caches them)
+        release = getattr(torch._C, "_host_emptyCache", None)
+        if release is not None:
+            release()
         if pipe is not None:
             serial = line["e2e"]
             line["e2e"] = {"value": world * upd / (pipe["ms_per_step"] / 1e3), "unit": "amp-updates/s",
