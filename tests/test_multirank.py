@@ -36,7 +36,7 @@ def _worker(rank, world, port, out):
 def test_aggregate_takes_the_slowest_rank_and_sums_the_work():
     world = 2
     port = _free_port()
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()   # no fork of a process that may hold OpenMP threads
     out = mgr.dict()
     mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
     for r in range(world):
