@@ -23,7 +23,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 
 def read_table(name):
     rows, cols = [], None
-    for line in open(os.path.join(HERE, "golden", name)):
+    with open(os.path.join(HERE, "golden", name)) as f:
+        lines = f.read().splitlines()
+    for line in lines:
         line = line.strip()
         if line.startswith("# p \\ sigma"):
             cols = [float(x) for x in line.split()[4:]]
