@@ -261,7 +261,11 @@ def e2e_pipelined(torch, qs, state, n, dtype, garr, n_gates, opts, k, dist, loca
         dt = max_over_ranks((time.perf_counter() - t0) / k, dist)
         clocks = sampler.stop()
         return {"ms_per_step": dt * 1e3, "steps": k, "pipelined": True, "states": 2, "streams": 2,
-                "clocks": clocks, "host_buffers_pinned": all(bool(h.is_pinned()) for h in hosts)}
+                "clocks": clocks, "host_buffers_pinned": all(bool(h.is_pinned()) for h in hosts),
+                "note": "every step copies its gate list in and its whole state out inside the timed region; "
+                        "a step's copy-out overlaps the next step's passes, and the two independent circuits "
+                        "overlap each other's pass tails, so this can come out below the single-stream "
+                        "device-timed step"}
     finally:
         # both streams idle before the second state goes and the first moves back
         L.qs_sync(other.handle)
