@@ -255,8 +255,11 @@ qs_status qs_qft(qs_state *s, int q0, int L, int inverse);
  * call the allocator at all).  The paper has no counterpart: this is a
  * service of the library, not a step of the method.
  *
- * dev_state: 2^n amplitudes of dtype dt in device memory (16-byte aligned);
- * dev_out: one double in device memory that receives sum_i |alpha_i|^2.
+ * dev_state: 2^n amplitudes of dtype dt in device memory (16-byte aligned
+ * for QS_C128, 8-byte for QS_C64); dev_out: one 8-byte aligned double in
+ * device memory that receives sum_i |alpha_i|^2.  Errors, detected before
+ * anything is launched: QS_EINVAL for a NULL or misaligned pointer or a bad
+ * dtype, QS_ERANGE for n < 1 or n > 32.
  * The call is enqueued on `stream` (NULL: legacy default stream) and returns
  * without waiting.  It calls no cudaMalloc, cudaFree or other allocating
  * routine: its partial sums (one per 2^16 amplitudes) live in a fixed
@@ -266,7 +269,10 @@ qs_status qs_qft(qs_state *s, int q0, int L, int inverse);
  * address (cudaGetSymbolAddress) with that device current, so make it before
  * any stream capture.  All calls share the array: calls that overlap on the
  * GPU (different streams, no ordering between them) race and may return
- * wrong sums; order them on one stream or with events. */
+ * wrong sums; order them on one stream or with events.  The sum is
+ * deterministic for a given n but may differ from qs_norm's in the last bits
+ * (the two reductions add in different orders).  The cached array address
+ * does not survive cudaDeviceReset: do not use the entry point across one. */
 qs_status qs_norm_noalloc(const void *dev_state, int n, qs_dtype dt, double *dev_out, void *stream);
 
 /* --------------------------------------------------------------------- */

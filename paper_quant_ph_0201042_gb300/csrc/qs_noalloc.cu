@@ -9,11 +9,17 @@
 // this library's device memory (loaded with the module, held by every GPU
 // that loads the library until the process exits).
 //
-// The reduction is a variant of the norm reduction of qs_reduce.cu: one
-// block per chunk of 2^16 amplitudes writes one double partial sum, then one
-// block adds the partials in a fixed order.  The scratch array holds at most
-// QS_NOALLOC_MAX_CHUNKS partials (1 MiB), so states of up to 2^32 amplitudes
-// are accepted.
+// The reduction is a variant of the norm reduction of qs_reduce.cu with a
+// different summation tree: one block per contiguous chunk of 2^16 amplitudes
+// writes one double partial sum, then one block adds the partials in a fixed
+// order.  The result is deterministic for a given n, but it may differ from
+// qs_norm's in the last bits, because qs_norm's first level strides over the
+// whole vector instead.  The scratch array holds at most 65536 partials
+// (1 MiB), so states of up to 2^32 amplitudes are accepted.
+//
+// The array's device address is resolved once per device and cached; a
+// cudaDeviceReset unloads the module, so the entry point must not be used
+// across a device reset (nor may the states it reads, which the reset frees).
 #include <mutex>
 
 #include "qs_internal.cuh"
@@ -92,6 +98,12 @@ qs_status scratch_address(int dev, double **out) {
 extern "C" qs_status qs_norm_noalloc(const void *dev_state, int n, qs_dtype dt, double *dev_out, void *stream) {
     if (!dev_state || !dev_out) return qs::fail(QS_EINVAL, "qs_norm_noalloc: NULL pointer");
     if (dt != QS_C64 && dt != QS_C128) return qs::fail(QS_EINVAL, "qs_norm_noalloc: bad dtype");
+    // the kernel reads float2 / double2 amplitudes and writes one double
+    const uintptr_t amp_align = dt == QS_C128 ? 16 : 8;
+    if (reinterpret_cast<uintptr_t>(dev_state) % amp_align)
+        return qs::fail(QS_EINVAL, dt == QS_C128 ? "qs_norm_noalloc: dev_state not 16-byte aligned"
+                                                 : "qs_norm_noalloc: dev_state not 8-byte aligned");
+    if (reinterpret_cast<uintptr_t>(dev_out) % 8) return qs::fail(QS_EINVAL, "qs_norm_noalloc: dev_out not 8-byte aligned");
     if (n < 1) return qs::fail(QS_ERANGE, "qs_norm_noalloc: n < 1");
     if (n > CHUNK_LOG + 16)
         return qs::fail(QS_ERANGE, "qs_norm_noalloc: n > 32 (its fixed scratch holds 65536 partial sums of "

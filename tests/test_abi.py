@@ -139,3 +139,22 @@ def test_plans_schedule_fewer_transposes_than_program_order(libpath):
     xp = sum(int(v) for v in re.findall(r"xpose=(\d+)", d))
     passes = len(re.findall(r"^pass ", d, flags=re.M))
     assert passes > 0 and xp < 1.6 * passes, (xp, passes)
+
+
+def test_norm_noalloc_rejects_bad_arguments_without_launching(libpath):
+    # every check runs on the host before any CUDA call, so fake device
+    # pointers are safe here: nothing is dereferenced or launched
+    L = qs.lib()
+    ok_state, ok_out = ctypes.c_void_p(1 << 20), ctypes.c_void_p(1 << 21)
+    assert L.qs_norm_noalloc(ok_state, 0, qs.QS_C64, ok_out, None) == 2            # QS_ERANGE: n < 1
+    assert L.qs_norm_noalloc(ok_state, 33, qs.QS_C128, ok_out, None) == 2          # QS_ERANGE: n > 32
+    assert L.qs_norm_noalloc(None, 10, qs.QS_C64, ok_out, None) == 1               # QS_EINVAL: NULL state
+    assert L.qs_norm_noalloc(ok_state, 10, qs.QS_C64, None, None) == 1             # QS_EINVAL: NULL result
+    assert L.qs_norm_noalloc(ok_state, 10, 7, ok_out, None) == 1                   # QS_EINVAL: bad dtype
+    # misaligned pointers: a complex128 state needs 16 bytes, complex64 8, the result 8
+    assert L.qs_norm_noalloc(ctypes.c_void_p((1 << 20) + 8), 10, qs.QS_C128, ok_out, None) == 1
+    assert b"16-byte" in L.qs_last_error()
+    assert L.qs_norm_noalloc(ctypes.c_void_p((1 << 20) + 4), 10, qs.QS_C64, ok_out, None) == 1
+    assert b"8-byte" in L.qs_last_error()
+    assert L.qs_norm_noalloc(ok_state, 10, qs.QS_C64, ctypes.c_void_p((1 << 21) + 4), None) == 1
+    assert b"dev_out" in L.qs_last_error()

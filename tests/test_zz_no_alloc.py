@@ -26,7 +26,8 @@ import workloads as W  # noqa: E402
 qbuild.build()
 
 
-@pytest.mark.parametrize("dtype,n", [("c128", 12), ("c64", 12), ("c64", 21), ("c128", 3)])
+@pytest.mark.parametrize("dtype,n", [("c128", 12), ("c64", 12), ("c64", 21), ("c128", 3), ("c128", 18),
+                                     ("c128", 20)])
 def test_norm_noalloc_matches_qs_norm(dtype, n):
     L = qs.lib()
     s = qs.State(n, dtype)
