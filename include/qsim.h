@@ -96,10 +96,20 @@ typedef struct {
  * (or NULL) selects the defaults. */
 typedef struct {
     int32_t no_fusion;       /* 1: one unfused pair-sweep launch per gate (the plain
-                                per-gate path); 0: fuse runs of gates into tile passes */
+                                per-gate path, double-precision instructions for a
+                                complex128 state); 0: fuse runs of gates into tile passes */
     int32_t max_ops_per_pass;/* 0: default */
-    int32_t reserved[6];
+    int32_t c128_arith;      /* arithmetic of the fused passes over a complex128 state:
+                                QS_ARITH_DEFAULT (0) or QS_ARITH_DS: double-single (each
+                                double split into two floats carrying 48 significant bits;
+                                products and sums by error-free transformations on the
+                                single-precision pipe; the state stays complex128 in
+                                memory); QS_ARITH_F64: double-precision instructions.
+                                Double-single needs n >= 10, else the passes use doubles. */
+    int32_t reserved[5];
 } qs_exec_opts;
+
+enum { QS_ARITH_DEFAULT = 0, QS_ARITH_F64 = 1, QS_ARITH_DS = 2 };
 
 /* --------------------------------------------------------------------- */
 /* State lifetime                                                          */

@@ -49,7 +49,10 @@ class QsGate(ctypes.Structure):
 
 class QsExecOpts(ctypes.Structure):
     _fields_ = [("no_fusion", ctypes.c_int32), ("max_ops_per_pass", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("c128_arith", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+
+
+ARITH = {"default": 0, "f64": 1, "ds": 2}
 
 
 class QsNoise(ctypes.Structure):
@@ -191,10 +194,11 @@ def gates_to_abi(gates: Sequence) -> ctypes.Array:
     return arr
 
 
-def _opts(fuse: bool, max_ops: int = 0) -> QsExecOpts:
+def _opts(fuse: bool, max_ops: int = 0, arith: str = "default") -> QsExecOpts:
     o = QsExecOpts()
     o.no_fusion = 0 if fuse else 1
     o.max_ops_per_pass = max_ops
+    o.c128_arith = ARITH[arith]
     return o
 
 
@@ -267,9 +271,10 @@ class State:
         check(lib().qs_apply_gate(self._h, arr))
         return self
 
-    def apply_circuit(self, gates: Sequence, fuse: bool = True, max_ops: int = 0):
+    def apply_circuit(self, gates: Sequence, fuse: bool = True, max_ops: int = 0, arith: str = "default"):
+        """arith (complex128 fused passes): 'default' / 'ds' double-single, 'f64' doubles."""
         arr = gates_to_abi(gates)
-        o = _opts(fuse, max_ops)
+        o = _opts(fuse, max_ops, arith)
         check(lib().qs_apply_circuit(self._h, arr, len(gates), ctypes.byref(o)))
         return self
 
@@ -336,11 +341,12 @@ class Plan:
     """A circuit compiled once (validation, fusion planning) for repeated
     execution on states of n qubits and the given dtype."""
 
-    def __init__(self, n: int, dtype: str, gates: Sequence, fuse: bool = True, max_ops: int = 0):
+    def __init__(self, n: int, dtype: str, gates: Sequence, fuse: bool = True, max_ops: int = 0,
+                 arith: str = "default"):
         self.n = n
         self.dtype = dtype
         arr = gates_to_abi(gates)
-        o = _opts(fuse, max_ops)
+        o = _opts(fuse, max_ops, arith)
         self._h = ctypes.c_void_p()
         check(lib().qs_plan_create(n, DTYPES[dtype], arr, len(gates), ctypes.byref(o),
                                    ctypes.byref(self._h)))

@@ -11,6 +11,9 @@ public API, beside the values the paper prints.
                transforms, for each error level alone, with the closed forms
   table_qft16  Table qft16od: fidelity of the 16-qubit QFT of Shor's
                period-finding step under both error kinds
+  GroverSearch Grover's search (Sec. 5.3) as fused plans, with a
+               double-precision renormalisation between plans for a
+               complex64 state
 
 Readings of the paper these runs take:
   * Table hod applies the transform k = 100 times and averages 10000 runs
@@ -62,6 +65,49 @@ PAPER_QFT16 = [[1.0000, 0.9999, 0.9999, 0.9999, 0.9998],
                [0.8837, 0.8897, 0.8827, 0.8801, 0.8980],
                [0.3287, 0.3399, 0.3332, 0.3209, 0.3363],
                [0.0027, 0.0015, 0.0019, 0.0017, 0.0031]]
+
+
+class GroverSearch:
+    """Grover's search (Sec. 5.3) on n qubits: H_n, then `iters` G-iterations
+    (V_{f_k}, H_n, V_{f_0}, H_n), compiled once as fused plans of at most
+    `renorm_every` iterations.  run() executes them from |0...0> and, between
+    plans and at the end, divides the state by its norm computed in double
+    precision (qs_renormalize): the single-precision rounding of a complex64
+    state drifts its norm by about 1e-5 over the 3216 iterations of n = 24,
+    which would push the success probability sin^2((2j+1) theta) above 1.
+    renorm_every = 0 (the default for complex128) compiles one plan."""
+
+    def __init__(self, n: int, marked: int, iters: int, dtype: str, renorm_every: int = None,
+                 arith: str = "default"):
+        if renorm_every is None:
+            renorm_every = 256 if dtype == "c64" else 0
+        self.n, self.marked, self.iters, self.dtype = n, marked, iters, dtype
+        self.renorm = renorm_every > 0
+        step = renorm_every if renorm_every > 0 else max(1, iters)
+        one = W.grover_circuit(n, marked, 1)[n:]          # one G-iteration
+        first = min(step, iters)
+        rest = iters - first
+        self.segments = [Plan(n, dtype, W.hadamard_layer(n) + one * first, arith=arith)]
+        if rest // step:
+            mid = Plan(n, dtype, one * step, arith=arith)
+            self.segments += [mid] * (rest // step)
+        if rest % step:
+            self.segments.append(Plan(n, dtype, one * (rest % step), arith=arith))
+        self.n_gates = n + iters * len(one)
+        self.launches = sum(p.launches for p in self.segments)
+
+    def run(self, state: State) -> State:
+        state.init_basis(0)
+        for p in self.segments:
+            p.execute(state)
+            if self.renorm:
+                state.renormalize()
+        return state
+
+    def closed_form(self) -> float:
+        """sin^2((2 iters + 1) theta), sin theta = 2^{-n/2}."""
+        th = math.asin(2.0 ** (-self.n / 2))
+        return math.sin((2 * self.iters + 1) * th) ** 2
 
 
 def _time(fn, reps: int = 3) -> float:

@@ -2,8 +2,14 @@
 same seeded inputs.
 
 Tolerances (||psi_gpu - psi_oracle||_2): 1e-12 for the complex128 state and
-1e-5 for the complex64 state at depth <= 500; longer circuits state their own
-bound in the test.  Reductions accumulate in double precision on both sides.
+1e-5 for the complex64 state at depth <= 500, the bounds the workloads fix;
+longer circuits state their own bound in the test.  Reductions accumulate in
+double precision on both sides.
+
+Fused complex128 passes run in double-single arithmetic by default (each
+double split into two floats, 48 significant bits, error-free products and
+sums); the tests run them and the double-precision passes ("f64") against the
+same bounds.
 """
 import math
 
@@ -21,6 +27,7 @@ if not torch.cuda.is_available():
 
 import paper_quant_ph_0201042_gb300 as qs  # noqa: E402
 from paper_quant_ph_0201042_gb300 import build as qbuild  # noqa: E402
+from paper_quant_ph_0201042_gb300 import paper  # noqa: E402
 
 qbuild.build()
 
@@ -28,13 +35,13 @@ TOL = {"c128": 1e-12, "c64": 1e-5}
 DTYPES = ["c128", "c64"]
 
 
-def gpu_run(n, gates, dtype, fuse=True, x0=0, psi=None, max_ops=0):
+def gpu_run(n, gates, dtype, fuse=True, x0=0, psi=None, max_ops=0, arith="default"):
     s = qs.State(n, dtype)
     if psi is not None:
         s.from_numpy(psi)
     else:
         s.init_basis(x0)
-    s.apply_circuit(gates, fuse=fuse, max_ops=max_ops)
+    s.apply_circuit(gates, fuse=fuse, max_ops=max_ops, arith=arith)
     out = s.to_numpy().astype(np.complex128)
     s.close()
     return out
@@ -55,7 +62,7 @@ def test_unfused_gates_every_kind(dtype, n):
     for g in gates:
         s.apply_gate(g)
     got = s.to_numpy().astype(np.complex128)
-    assert err(got, want) < TOL[dtype] * (1 if dtype == "c128" else 2)
+    assert err(got, want) < TOL[dtype]
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
@@ -80,33 +87,37 @@ def test_entry_points(dtype):
     assert err(s.to_numpy().astype(np.complex128), ref) < TOL[dtype]
 
 
-@pytest.mark.parametrize("dtype", DTYPES)
+# (dtype, arithmetic of the fused complex128 passes)
+VARIANTS = [("c128", "ds"), ("c128", "f64"), ("c64", "default")]
+
+
+@pytest.mark.parametrize("dtype,arith", VARIANTS)
 @pytest.mark.parametrize("n", [9, 10, 11, 12, 13, 14, 16, 17])
-def test_fused_random_circuits(dtype, n):
+def test_fused_random_circuits(dtype, arith, n):
     r = W.rng(2000 + n)
     for trial in range(3):
         gates = [random_gate(r, n) for _ in range(150)]
         psi = random_state(r, n)
         want = oracle.run(n, gates, psi=psi)
-        got = gpu_run(n, gates, dtype, fuse=True, psi=psi)
-        assert err(got, want) < TOL[dtype] * (1 if dtype == "c128" else 3), trial
+        got = gpu_run(n, gates, dtype, fuse=True, psi=psi, arith=arith)
+        assert err(got, want) < TOL[dtype], trial
 
 
-@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("dtype,arith", VARIANTS)
 @pytest.mark.parametrize("max_ops", [4, 7, 16])
-def test_fused_small_passes(dtype, max_ops):
+def test_fused_small_passes(dtype, arith, max_ops):
     # many short passes, transposes at pass edges
     n = 13
     r = W.rng(31 + max_ops)
     gates = [random_gate(r, n, max_ctrl=2) for _ in range(120)]
     psi = random_state(r, n)
     want = oracle.run(n, gates, psi=psi)
-    got = gpu_run(n, gates, dtype, fuse=True, psi=psi, max_ops=max_ops)
-    assert err(got, want) < TOL[dtype] * (1 if dtype == "c128" else 3)
+    got = gpu_run(n, gates, dtype, fuse=True, psi=psi, max_ops=max_ops, arith=arith)
+    assert err(got, want) < TOL[dtype]
 
 
-@pytest.mark.parametrize("dtype", DTYPES)
-def test_fused_high_qubit_only_and_lane_only(dtype):
+@pytest.mark.parametrize("dtype,arith", VARIANTS)
+def test_fused_high_qubit_only_and_lane_only(dtype, arith):
     n = 15
     r = W.rng(5)
     psi = random_state(r, n)
@@ -114,7 +125,23 @@ def test_fused_high_qubit_only_and_lane_only(dtype):
     lane = [W.Gate("MATRIX", q, matrix=W.haar_su2(r)) for q in range(10, 15)] * 3
     for gates in (high, lane, high + lane + high):
         want = oracle.run(n, gates, psi=psi)
-        assert err(gpu_run(n, gates, dtype, psi=psi), want) < TOL[dtype]
+        assert err(gpu_run(n, gates, dtype, psi=psi, arith=arith), want) < TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype,arith", VARIANTS)
+def test_fused_every_gate_class(dtype, arith):
+    # every kind with controls inside and outside the tile, Hadamard
+    # butterflies (an odd count, so the folded factor is not a power of two),
+    # diagonal gates with an exact-1 entry, SWAPs; a random state so that no
+    # amplitude is zero
+    n = 14
+    r = W.rng(606)
+    psi = random_state(r, n)
+    gates = [random_gate(r, n, max_ctrl=2) for _ in range(200)]
+    gates += [W.Gate("H", q) for q in (0, 3, 9, 12, 13)]
+    gates += [W.Gate("UP1", q, angles=(0.3 * q,), controls={(q + 5) % n: 1}) for q in range(n)]
+    want = oracle.run(n, gates, psi=psi)
+    assert err(gpu_run(n, gates, dtype, psi=psi, arith=arith), want) < TOL[dtype]
 
 
 def test_qft_n10_closed_form():
@@ -165,7 +192,7 @@ def test_grover_n12_full_state(dtype):
     gates = W.grover_circuit(n, k, it)
     want = oracle.run(n, gates)
     got = gpu_run(n, gates, dtype)
-    assert err(got, want) < (1e-11 if dtype == "c128" else 1e-4)
+    assert err(got, want) < (1e-11 if dtype == "c128" else 1e-5)
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
@@ -176,24 +203,55 @@ def test_grover_n24_success_probability(dtype):
     k = W.basis_index(24, n)
     it = W.grover_iterations(n)
     assert it == 3216
-    s = qs.State(n, dtype).init_basis(0)
-    s.apply_circuit(W.grover_circuit(n, k, it))
+    # complex64: a double-precision renormalisation every 256 iterations
+    search = paper.GroverSearch(n, k, it, dtype)
+    s = search.run(qs.State(n, dtype))
     th = math.asin(2.0 ** (-n / 2))
     want = math.sin((2 * it + 1) * th) ** 2
+    assert want == search.closed_form()
     p = s.prob(k)
-    tol = 1e-9 if dtype == "c128" else 2e-3
+    tol = 1e-9 if dtype == "c128" else 1e-5
     assert abs(p - want) < tol, (p, want)
-    assert abs(s.norm() - 1) < (1e-9 if dtype == "c128" else 1e-2)
+    assert p <= 1 + 1e-7
+    assert abs(s.norm() - 1) < (1e-9 if dtype == "c128" else 1e-5)
 
 
-@pytest.mark.parametrize("dtype", DTYPES)
-def test_random_circuit_n20_oracle(dtype):
+def test_grover_n24_complex64_drifts_without_renormalisation():
+    # the same search as one plan, no renormalisation: the norm drifts by
+    # the accumulated single-precision rounding, which the renormalising run
+    # above removes
+    n = 24
+    k = W.basis_index(24, n)
+    it = W.grover_iterations(n)
+    s = paper.GroverSearch(n, k, it, "c64", renorm_every=0).run(qs.State(n, "c64"))
+    drift = abs(s.norm() - 1)
+    assert 1e-7 < drift < 1e-3, drift
+
+
+@pytest.mark.parametrize("dtype,arith", VARIANTS)
+def test_random_circuit_n20_oracle(dtype, arith):
     # the 40-layer random circuit of the throughput workload at n = 20
     n = 20
     gates = W.random_circuit(n, 40, seed=7)
     want = oracle.run(n, gates)
-    got = gpu_run(n, gates, dtype)
-    assert err(got, want) < (1e-12 if dtype == "c128" else 2e-5)
+    got = gpu_run(n, gates, dtype, arith=arith)
+    assert err(got, want) < TOL[dtype]
+
+
+@pytest.fixture(scope="module")
+def oracle_n26():
+    # the throughput workload's generator at n = 26, 10 layers (390 gates):
+    # the largest register the oracle runs in test time (1 GiB complex128)
+    n = 26
+    gates = W.random_circuit(n, 10, seed=11)
+    return n, gates, oracle.run(n, gates)
+
+
+@pytest.mark.parametrize("dtype,arith", VARIANTS)
+def test_random_circuit_n26_oracle(oracle_n26, dtype, arith):
+    n, gates, want = oracle_n26
+    got = gpu_run(n, gates, dtype, arith=arith)
+    assert err(got, want) < TOL[dtype]
 
 
 def test_random_circuit_n30_full_size():
@@ -210,7 +268,7 @@ def test_random_circuit_n30_full_size():
     qs.Plan(n, "c128", gates).execute(s128)
     assert abs(s128.norm() - 1) < 1e-11
     d = (s64.tensor.to(torch.complex128) - s128.tensor).abs().pow(2).sum().sqrt().item()
-    assert d < 2e-5, d
+    assert d < 1e-5, d
     del s64
     # U^dagger U |0> = |0>
     inv = []
