@@ -434,6 +434,59 @@ qs_status qs_adjoint_grad_ex(qs_state *s, const qs_gate *g, size_t m, const doub
 qs_status qs_adjoint_describe(int n, qs_dtype dt, const qs_gate *g, size_t m, char *buf, size_t len, size_t *needed);
 
 /* --------------------------------------------------------------------- */
+/* A register partitioned over 2^g ranks (Sec. 2.2.1: the overall matrix    */
+/* splits into independent blocks M_k = S_k phi_k, spread here over GPUs)   */
+/* --------------------------------------------------------------------- */
+
+/* Partition: qubits 0 .. g-1 (the g most significant index bits) are
+ * "global" and name the rank; rank r holds the 2^(n-g) amplitudes whose top
+ * g bits equal r, as a state of n-g qubits (its qubit j is qubit g+j of the
+ * register).
+ *
+ * qs_shard_plan rewrites gates g[0..m-1] (qubits of the register) into the
+ * physical numbering of the partition: an uncontrolled SWAP of the circuit
+ * renames qubits (no data moves), a controlled SWAP becomes three C-NOTs,
+ * and before every non-diagonal gate whose target sits on a global qubit an
+ * exchange is inserted: an uncontrolled QS_GATE_SWAP with t < g <= t2, which
+ * swaps the global qubit t with the local qubit t2 (the local qubit chosen
+ * is the one whose next non-diagonal use lies furthest ahead).  Every other
+ * output gate has the input's kind, angles and matrix with its qubits
+ * renamed; its controls may be global, and its target is global only for a
+ * diagonal gate.  final_pos (n entries, may be NULL) receives the physical
+ * qubit of each logical qubit after the last gate.  out may be NULL (count
+ * only); *n_out receives the number of output gates, and QS_ERANGE is
+ * returned if it exceeds max_out.  Needs n - g >= 2 (QS_ERANGE), valid gates
+ * (QS_EINVAL).  Host only: no GPU needed.
+ *
+ * An exchange SWAP(t, t2) on rank r, with b = bit (g-1-t) of r and partner
+ * r ^ (1 << (g-1-t)): the rank sends the half of its slice whose local qubit
+ * t2-g equals 1-b and receives the partner's half (whose local qubit equals
+ * b on the partner) into the same places, i.e. qs_shard_pack(s, t2-g, 1-b,
+ * send), transport, qs_shard_unpack(s, t2-g, 1-b, recv).
+ *
+ * qs_shard_localize converts physical gates without exchanges (a stretch
+ * between two of them) into rank `rank`'s gates on its (n-g)-qubit slice:
+ * gates whose global controls this rank does not meet are dropped, global
+ * controls it meets are removed, a diagonal gate on a global qubit becomes
+ * the scalar (its entry for this rank's bit) on the slice's amplitudes that
+ * meet the local controls (a QS_GATE_MATRIX diag(d, d), or diag on a control
+ * qubit if every local qubit is a control); entries exactly 1 are dropped.
+ * QS_EINVAL for an exchange or a non-diagonal gate on a global qubit.
+ * Output sizing as for qs_shard_plan.  Host only. */
+qs_status qs_shard_plan(int n, int g, const qs_gate *gates, size_t m, qs_gate *out, size_t max_out, size_t *n_out,
+                        int32_t *final_pos);
+qs_status qs_shard_localize(int n, int g, uint32_t rank, const qs_gate *in, size_t m, qs_gate *out, size_t max_out,
+                            size_t *n_out);
+
+/* Copies the 2^(n-1) amplitudes of s whose qubit q equals value (0 or 1), in
+ * index order, into the device buffer dev_buf (qs_shard_pack), or writes
+ * them back from it (qs_shard_unpack); asynchronous on the state's stream.
+ * dev_buf must hold 2^(n-1) amplitudes of the state's dtype and be aligned
+ * to one amplitude (QS_EINVAL otherwise, and for q out of range). */
+qs_status qs_shard_pack(qs_state *s, int q, int value, void *dev_buf);
+qs_status qs_shard_unpack(qs_state *s, int q, int value, const void *dev_buf);
+
+/* --------------------------------------------------------------------- */
 /* Host copies (checkpoint / restore)                                      */
 /* --------------------------------------------------------------------- */
 

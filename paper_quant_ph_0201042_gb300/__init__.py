@@ -131,6 +131,12 @@ _SIGS = {
                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(QsExecOpts)],
     "qs_adjoint_describe": [ctypes.c_int, ctypes.c_int, ctypes.POINTER(QsGate), ctypes.c_size_t, ctypes.c_char_p,
                             ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)],
+    "qs_shard_plan": [ctypes.c_int, ctypes.c_int, ctypes.POINTER(QsGate), ctypes.c_size_t, ctypes.POINTER(QsGate),
+                      ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_int32)],
+    "qs_shard_localize": [ctypes.c_int, ctypes.c_int, ctypes.c_uint32, ctypes.POINTER(QsGate), ctypes.c_size_t,
+                          ctypes.POINTER(QsGate), ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)],
+    "qs_shard_pack": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p],
+    "qs_shard_unpack": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p],
     "qs_copy_out": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t],
     "qs_copy_out_async": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t],
     "qs_sync": [ctypes.c_void_p],

@@ -131,6 +131,31 @@ QS_HD double join(float h, float l) {
 // dropped (2^-48 of its term).
 QS_HD void dot4(const float (&ah)[4], const float (&al)[4], const float (&bh)[4], const float (&bl)[4], float &h,
                 float &l) {
+#ifndef QS_DS_CHAIN
+    // pairwise: the high products summed as (p0 + p1) + (p2 + p3), the
+    // low-order terms in two independent chains, for instruction-level
+    // parallelism
+    float p[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) p[k] = mul(ah[k], bh[k]);
+    float la = fma(ah[0], bh[0], -p[0]), lb = fma(ah[2], bh[2], -p[2]);
+    la = fma(ah[0], bl[0], la);
+    lb = fma(ah[2], bl[2], lb);
+    la = fma(al[0], bh[0], la);
+    lb = fma(al[2], bh[2], lb);
+    la = add(la, fma(ah[1], bh[1], -p[1]));
+    lb = add(lb, fma(ah[3], bh[3], -p[3]));
+    la = fma(ah[1], bl[1], la);
+    lb = fma(ah[3], bl[3], lb);
+    la = fma(al[1], bh[1], la);
+    lb = fma(al[3], bh[3], lb);
+    float s01, r01, s23, r23, s, r;
+    two_sum(p[0], p[1], s01, r01);
+    two_sum(p[2], p[3], s23, r23);
+    two_sum(s01, s23, s, r);
+    const float lo = add(add(la, lb), add(add(r01, r23), r));
+    fast_two_sum(s, lo, h, l);
+#else
     float p[4], lo;
 #pragma unroll
     for (int k = 0; k < 4; ++k) p[k] = mul(ah[k], bh[k]);
@@ -150,6 +175,7 @@ QS_HD void dot4(const float (&ah)[4], const float (&al)[4], const float (&bh)[4]
     two_sum(s, p[3], s, r);
     lo = add(lo, r);
     fast_two_sum(s, lo, h, l);
+#endif
 }
 
 // Sum of two terms a0*b0 + a1*b1, renormalised.

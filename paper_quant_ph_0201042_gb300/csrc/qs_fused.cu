@@ -35,13 +35,44 @@
 #include <set>
 
 #include "qs_internal.cuh"
-#include "qs_ds.cuh"
-#include "qs_pass.cuh"
 
 namespace qs {
 
 namespace {
 
+constexpr int LB = 5;          // lane bits
+#ifndef QS_MAX_WB
+#define QS_MAX_WB 3
+#endif
+constexpr int MAX_WB = QS_MAX_WB;  // warp bits (2^MAX_WB warps per CTA)
+constexpr int MAX_OPS = 120;   // ops per pass (shared-memory op table)
+#ifndef QS_RB64
+#define QS_RB64 5
+#endif
+#ifndef QS_WB64
+#define QS_WB64 3
+#endif
+#ifndef QS_RB128
+#define QS_RB128 4
+#endif
+#ifndef QS_FUSED_MINBLOCKS
+#define QS_FUSED_MINBLOCKS 2
+#endif
+constexpr int RB64 = QS_RB64;      // complex64: 2^RB64 amplitudes per thread
+constexpr int WB64 = QS_WB64;      // complex64: 2^WB64 warps per CTA
+constexpr int RB128 = QS_RB128;    // complex128: 2^RB128 amplitudes per thread
+// a layout packs RB + WB slots of 4 bits into 32 bits; a control mask over
+// the register index is 8 bits wide
+static_assert(RB64 + WB64 <= 8 && RB128 + MAX_WB <= 8, "layout does not fit 32 bits");
+static_assert(RB64 <= 5 && RB128 <= 5 && MAX_WB <= 4, "register or warp bits out of range");
+
+enum OpType : uint8_t { OP_REG = 0, OP_LANE = 1, OP_DIAG = 2, OP_XPOSE = 3 };
+
+// Fused-only gate class: an uncontrolled Hadamard applied as the butterfly
+// (x + y, x - y); the factors 1/sqrt 2 of all such gates of a pass are folded
+// into one scale at the store (exact when their number is even, so a complex64
+// register does not drift by the rounding of 1/sqrt 2 once per gate).
+constexpr int GC_HB = 8;
 
 template <typename R>
 struct alignas(16) FOp {
@@ -356,6 +387,43 @@ __global__ void __launch_bounds__(32 << QS_MAX_WB, 1) k_fused(cplx<R> *__restric
 // scattering.
 // ---------------------------------------------------------------------------
 
+// One op of the complex64 kernel (112 bytes).
+struct alignas(16) POp {
+    uint8_t type, cls, tsel, tpos;
+    uint8_t rmask, rval;
+    uint8_t fast;          // state-vector fast paths: 1 uncontrolled general gate on a register slot,
+                           // 2 X deferred into the index mask, 3 uncontrolled general gate on a lane bit
+    uint8_t pad0;
+    uint32_t pad1;
+    uint16_t tmask, tval;
+    uint64_t omask, oval;
+    // OP_REG / OP_LANE: u00, u01, u10, u11 in c[0..3]; OP_DIAG: d0, d1 in c[0..1]
+    // OP_XPOSE: 32 uint16 read offsets (old tile order) of the new register
+    //           indices in c[0..7], then the old tile-order bit of each new
+    //           warp bit (bytes) in c[8..9]
+    float2 c[10];
+};
+static_assert(sizeof(POp) == 112, "POp layout");
+
+struct PassC64 {
+    const POp *ops;
+    uint64_t tiles;
+    int32_t K, WB, nops, has_xpose;
+    float scale;
+    int32_t n;                         // qubits (trajectory mode: state stride 2^n)
+    // trajectory mode: per-(trajectory, op) records; trajectory b's record of
+    // op k of this pass is recs[b * rec_stride + rec_off + k]
+    const TrajRec *recs;
+    uint64_t tiles_per_traj;
+    uint32_t rec_stride, rec_off;
+    uint8_t tile_pos[24];
+    uint64_t ld_reg[32], ld_warp[4];   // global offsets of register index j / warp bit w (first layout)
+    uint64_t st_reg[32], st_warp[4];   // the same for the last layout (store)
+};
+
+__device__ __forceinline__ bool lpred(int j, uint32_t xm, int rm, int rv) {
+    return ((uint32_t(j) ^ xm) & uint32_t(rm)) == uint32_t(rv);
+}
 
 // (x, y) <- (u00 x + u01 y, u10 x + u11 y) in place.  The four output chains
 // run in lockstep and each ends on the input it replaces (x.re, x.im, y.re,
@@ -761,13 +829,13 @@ struct Plan {
     int n = 0;
     qs_dtype dt = QS_C64;
     bool fused = false;
-    bool ds = false;                         // complex128 passes in double-single arithmetic (qs_fused_ds.cu)
+    DsPlan *dsp = nullptr;                   // complex128 passes in double-single arithmetic (qs_fused_ds.cu)
     std::vector<HostOp> ops;                 // unfused mode
     std::vector<PassDesc<float>> pf;         // fused passes, complex64
     std::vector<PassDesc<double>> pd;        // fused passes, complex128
     std::vector<std::vector<FOp<float>>> of; // op tables of the passes (host)
-    std::vector<PassC64> pc;                 // complex64 / double-single kernel descriptors
-    std::vector<std::vector<POp>> pco;       // their op tables (host)
+    std::vector<PassC64> pc;                 // complex64 kernel descriptors
+    std::vector<std::vector<POp>> pco;       // complex64 kernel op tables (host)
     std::vector<std::vector<FOp<double>>> od;
     void *dev_ops = nullptr;                 // all op tables (device), owned
     bool temp = false;                       // stream-ordered table (one-shot plan)
@@ -783,6 +851,7 @@ struct Plan {
     size_t ev_used = 0;
 
     ~Plan() {
+        if (dsp) ds_plan_destroy(dsp);
         for (cudaEvent_t e : ev) cudaEventDestroy(e);
         if (dev_ops) {
             if (temp) cudaFreeAsync(dev_ops, free_stream);
@@ -1100,6 +1169,10 @@ std::vector<PlannedPass> form_passes(int n, int H, int max_ops, const std::vecto
 
 }  // namespace
 
+void expand_swap_ops(const std::vector<HostOp> &in, std::vector<HostOp> &out) { expand_swaps(in, out); }
+
+cudaError_t plan_mark(Plan *p, cudaStream_t st, bool end) { return p ? p->mark(st, end) : cudaSuccess; }
+
 std::vector<PassGroup> group_passes(int n, int H, int max_ops, const std::vector<HostOp> &ops) {
     std::vector<PlannedPass> pp = form_passes(n, H, max_ops, ops);
     std::vector<PassGroup> out(pp.size());
@@ -1210,23 +1283,15 @@ int lay_slot(uint32_t lay, int s) { return int((lay >> (4 * s)) & 15u); }
 // Complex64 kernel descriptor and op table from a planned pass: coefficient
 // vectors for FFMA2, global offsets of the first and last layouts, and the
 // read pattern of every transpose.
-//
-// With R = double the pass is for the double-single kernel: every matrix
-// entry and the folded Hadamard factor are split into a high float and a low
-// float (c[0..3] high parts, c[4..7] low parts), so the kernel sees the
-// double-precision matrix to 48 bits.
-template <typename R>
-void convert_pass(const PassDesc<R> &D, const std::vector<FOp<R>> &ops, PassC64 &out, std::vector<POp> &pops) {
+void convert_c64(const PassDesc<float> &D, const std::vector<FOp<float>> &ops, PassC64 &out, std::vector<POp> &pops) {
     constexpr int RB = RB64;
-    constexpr bool DS = sizeof(R) == 8;
     std::memset(&out, 0, sizeof(out));
     out.tiles = D.tiles;
     out.K = D.K;
     out.WB = D.WB;
     out.nops = D.nops;
     out.has_xpose = D.has_xpose;
-    if (DS) ds::split_const(double(D.scale), out.scale, out.scale_lo);
-    else out.scale = float(D.scale);
+    out.scale = D.scale;
     std::memcpy(out.tile_pos, D.tile_pos, sizeof(out.tile_pos));
     const int WB = D.WB;
     auto offsets = [&](uint32_t lay, uint64_t *reg, uint64_t *warp) {
@@ -1242,7 +1307,7 @@ void convert_pass(const PassDesc<R> &D, const std::vector<FOp<R>> &ops, PassC64 
     offsets(lay, out.ld_reg, out.ld_warp);
     pops.assign(ops.size(), POp{});
     for (size_t k = 0; k < ops.size(); ++k) {
-        const FOp<R> &f = ops[k];
+        const FOp<float> &f = ops[k];
         POp &q = pops[k];
         q.type = f.type; q.cls = f.cls; q.tsel = f.tsel; q.tpos = f.tpos;
         q.rmask = f.rmask; q.rval = f.rval; q.tmask = f.tmask; q.tval = f.tval;
@@ -1274,26 +1339,14 @@ void convert_pass(const PassDesc<R> &D, const std::vector<FOp<R>> &ops, PassC64 
             for (int w = 0; w < WB; ++w) ow[w] = uint8_t(oldpos[lay_slot(nl, RB + w)]);
             std::memcpy(&q.c[8], ow, sizeof(ow));
             lay = nl;
+        } else if (f.type == OP_DIAG) {
+            q.c[0] = make_float2(f.u[0], f.u[1]);
+            q.c[1] = make_float2(f.u[2], f.u[3]);
         } else {
-            const int ne = f.type == OP_DIAG ? 2 : 4;   // (d0, d1) or u00, u01, u10, u11
-            for (int e = 0; e < ne; ++e) {
-                if (DS) {
-                    float rh, rl, ih, il;
-                    ds::split_const(double(f.u[2 * e]), rh, rl);
-                    ds::split_const(double(f.u[2 * e + 1]), ih, il);
-                    q.c[e] = make_float2(rh, ih);
-                    q.c[4 + e] = make_float2(rl, il);
-                } else {
-                    q.c[e] = make_float2(float(f.u[2 * e]), float(f.u[2 * e + 1]));
-                }
-            }
+            for (int e = 0; e < 4; ++e) q.c[e] = make_float2(f.u[2 * e], f.u[2 * e + 1]);
         }
     }
     offsets(lay, out.st_reg, out.st_warp);
-}
-
-void convert_c64(const PassDesc<float> &D, const std::vector<FOp<float>> &ops, PassC64 &out, std::vector<POp> &pops) {
-    convert_pass<float>(D, ops, out, pops);
 }
 
 cudaError_t ensure_device_c64(Plan *P, cudaStream_t st) {
@@ -1318,19 +1371,17 @@ cudaError_t ensure_device_c64(Plan *P, cudaStream_t st) {
     }
     if (e != cudaSuccess) return e;
     for (size_t k = 0; k < P->pc.size(); ++k) P->pc[k].ops = static_cast<const POp *>(P->dev_ops) + offs[k];
-    static int grid_cache[2][64] = {};
+    static int grid_cache[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
-    int &g = grid_cache[P->ds ? 1 : 0][dev & 63];
+    int &g = grid_cache[dev & 63];
     if (g == 0) {
         int sms = 0, per_sm = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const size_t amp = P->ds ? 16 : 8;   // transpose buffer: float4 / float2 per amplitude
-        const size_t smem_max = (amp << (LB + RB64 + WB64)) + MAX_OPS * sizeof(POp);
-        const void *kern = P->ds ? fused_ds_kernel() : reinterpret_cast<const void *>(&k_fused_c64<false>);
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_max));
+        const size_t smem_max = (size_t(8) << (LB + RB64 + WB64)) + MAX_OPS * sizeof(POp);
+        e = cudaFuncSetAttribute(k_fused_c64<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_max));
         if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 << WB64, smem_max);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_c64<false>, 32 << WB64, smem_max);
         if (e != cudaSuccess) return e;
         g = std::max(1, sms * std::max(1, per_sm));
     }
@@ -1340,16 +1391,11 @@ cudaError_t ensure_device_c64(Plan *P, cudaStream_t st) {
 
 cudaError_t run_passes_c64(qs_state *s, Plan *P) {
     for (const PassC64 &D : P->pc) {
-        const size_t smem = (D.has_xpose ? (size_t(P->ds ? 16 : 8) << D.K) : 0) + size_t(D.nops) * sizeof(POp);
+        const size_t smem = (D.has_xpose ? (size_t(8) << D.K) : 0) + size_t(D.nops) * sizeof(POp);
         const uint64_t grid = std::min<uint64_t>(D.tiles, uint64_t(P->grid));
         cudaError_t e = P->mark(s->stream, false);
         if (e != cudaSuccess) return e;
-        if (P->ds) {
-            e = launch_fused_ds(unsigned(grid), 32u << D.WB, smem, s->stream, static_cast<double2 *>(s->d), D);
-            if (e != cudaSuccess) return e;
-        } else {
-            k_fused_c64<false><<<unsigned(grid), 32u << D.WB, smem, s->stream>>>(static_cast<float2 *>(s->d), D);
-        }
+        k_fused_c64<false><<<unsigned(grid), 32u << D.WB, smem, s->stream>>>(static_cast<float2 *>(s->d), D);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         e = P->mark(s->stream, true);
@@ -1367,26 +1413,27 @@ qs_status plan_build(int n, qs_dtype dt, const std::vector<HostOp> &ops, const q
     P->n = n;
     P->dt = dt;
     P->n_gates = int64_t(ops.size());
-    // complex128: double-single passes unless the caller asks for double-precision instructions
-    P->ds = dt == QS_C128 && o.c128_arith != QS_ARITH_F64 && n >= LB + RB64;
-    P->RB = (dt == QS_C64 || P->ds) ? RB64 : RB128;
+    P->RB = dt == QS_C64 ? RB64 : RB128;
     const int max_ops = o.max_ops_per_pass > 0 ? std::max(4, std::min(o.max_ops_per_pass, MAX_OPS)) : MAX_OPS;
     P->fused = !o.no_fusion && n >= LB + P->RB;
+    // complex128: double-single passes (n >= 12) unless the caller asks for
+    // double-precision instructions
+    const bool ds = dt == QS_C128 && o.c128_arith != QS_ARITH_F64 && n >= 12;
     if (!P->fused) {
-        P->ds = false;
         P->ops = ops;
+    } else if (ds) {
+        qs_status st = ds_plan_build(n, ops, o.max_ops_per_pass, temp, &P->dsp);
+        if (st != QS_OK) {
+            delete P;
+            return st;
+        }
     } else {
         qs_status st = dt == QS_C64 ? build_fused<float, RB64>(P, ops, max_ops, P->pf, P->of)
-                       : P->ds      ? build_fused<double, RB64>(P, ops, max_ops, P->pd, P->od)
                                     : build_fused<double, RB128>(P, ops, max_ops, P->pd, P->od);
         if (st == QS_OK && dt == QS_C64) {
             P->pc.resize(P->pf.size());
             P->pco.resize(P->pf.size());
             for (size_t k = 0; k < P->pf.size(); ++k) convert_c64(P->pf[k], P->of[k], P->pc[k], P->pco[k]);
-        } else if (st == QS_OK && P->ds) {
-            P->pc.resize(P->pd.size());
-            P->pco.resize(P->pd.size());
-            for (size_t k = 0; k < P->pd.size(); ++k) convert_pass<double>(P->pd[k], P->od[k], P->pc[k], P->pco[k]);
         }
         if (st != QS_OK) {
             delete P;
@@ -1408,7 +1455,9 @@ qs_status plan_run(qs_state *s, Plan *p) {
             if (e == cudaSuccess) e = p->mark(s->stream, true);
             if (e != cudaSuccess) break;
         }
-    } else if (s->dt == QS_C64 || p->ds) {
+    } else if (p->dsp) {
+        e = ds_plan_run(p->dsp, static_cast<double2 *>(s->d), s->stream, p);
+    } else if (s->dt == QS_C64) {
         e = ensure_device_c64(p, s->stream);
         if (e == cudaSuccess) e = run_passes_c64(s, p);
     } else {
@@ -1428,7 +1477,7 @@ void plan_counts(const Plan *p, int64_t *launches, int64_t *gates) {
             for (const HostOp &o : p->ops) c += o.cls == GC_ID ? 0 : 1;
             *launches = c;
         } else {
-            *launches = int64_t(p->dt == QS_C64 ? p->pf.size() : p->pd.size());
+            *launches = p->dsp ? ds_plan_launches(p->dsp) : int64_t(p->dt == QS_C64 ? p->pf.size() : p->pd.size());
         }
     }
     if (gates) *gates = p->n_gates;
@@ -1494,9 +1543,10 @@ std::string plan_describe(const Plan *p) {
     char head[160];
     std::snprintf(head, sizeof(head), "plan: n=%d dtype=%s gates=%lld fused=%d arith=%s\n", p->n,
                   p->dt == QS_C64 ? "c64" : "c128", (long long)p->n_gates, int(p->fused),
-                  p->dt == QS_C64 ? "f32" : (p->ds ? "double-single" : "f64"));
+                  p->dt == QS_C64 ? "f32" : (p->dsp ? "double-single" : "f64"));
     out += head;
     if (!p->fused) return out;
+    if (p->dsp) return out + ds_plan_describe(p->dsp);
     if (p->dt == QS_C64) describe_passes<float>(p->pf, p->of, p->order, out);
     else describe_passes<double>(p->pd, p->od, p->order, out);
     // the planned ops (forward matrices, (re, im) row-major)

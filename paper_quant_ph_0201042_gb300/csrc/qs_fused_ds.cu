@@ -1,341 +1,396 @@
-// Fused pass over a complex128 state in double-single arithmetic.
+// Fused passes over a complex128 state in double-single arithmetic.
 //
-// The same pass as the complex64 kernel of qs_fused.cu (tile of 2^13
-// amplitudes: 5 lane bits and 8 high bits; 32 amplitudes per thread in
-// registers; lane partners by __shfl_xor_sync; transposes through shared
-// memory; C-NOTs on register slots deferred into an index mask; every
-// layout-dependent offset tabulated on the host), with two differences:
+// A pass groups consecutive gates whose targets lie in a tile of 2^12
+// amplitudes (the five lowest index bits, so that global loads and stores are
+// contiguous 512-byte rows, plus seven higher bits chosen per pass) and
+// applies all of them to the tile in shared memory: one HBM read and one
+// write of the state per pass.  The tile is the paper's block M_k (Sec.
+// 2.2.1) generalised to any set of fixed index bits.
 //
-//  * the state in memory is complex128; each amplitude is split at the load
-//    into two float pairs (re = rh + rl, im = ih + il, 48 significant bits)
-//    and joined back into doubles at the store, with integer instructions;
-//  * every gate runs in double-single arithmetic (qs_ds.cuh): products of
-//    the high parts are exact pairs, sums of them exact pairs, and the
-//    low-order terms are added in single precision.  The gate matrices come
-//    from the double-precision matrices of the plan, split into high and low
-//    floats on the host.
+// Number format: the state stays complex128 in memory (the paper's double
+// precision, Sec. 2.1).  At the load each amplitude is split into two float
+// pairs (re = rh + rl, im = ih + il, 48 significant bits) with integer
+// instructions, the gates run in double-single arithmetic (qs_ds.cuh: exact
+// products and sums of the high parts by error-free transformations, low
+// parts in single precision) on the single-precision pipe, and the store
+// joins the pairs back into doubles.  Gate matrices come from the plan's
+// double-precision matrices, split on the host.
 //
-// The arithmetic of the pair update (Sec. 2.2.1: x' = u11 x + u12 y,
-// y' = u21 x + u22 y) is the same; only the number format differs.  One CTA
-// of 256 threads per SM (128 registers of state per thread; a 128 KiB
-// transpose buffer).
+// The tile lives in shared memory (16 bytes per amplitude, float4), not in
+// registers: a gate is a runtime loop over the pairs of the tile, so its
+// code is a few hundred instructions whatever the target bit, and any tile
+// bit can be a target without a transpose.  Per op:
+//   * general or real 2x2 on tile bit t (Sec. 2.2.1: x' = u11 x + u12 y,
+//     y' = u21 x + u22 y), with controls as a predicate on the pair's index
+//     (tile bits) or on the tile's position (other bits), Sec. 2.2.2;
+//   * an uncontrolled Hadamard as the butterfly (x + y, x - y), the factors
+//     1/sqrt 2 of a pass folded into one scale at the store;
+//   * a diagonal gate on the amplitudes it changes (only one side of the
+//     target when the other entry is exactly 1);
+//   * a C-NOT without controls on tile bits moves no data: the tile keeps an
+//     XOR mask, and logical index i sits at place i ^ mask.
+// 256 threads per CTA, three CTAs per SM (shared memory), so that one CTA's
+// HBM phase overlaps the others' arithmetic.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
 #include "qs_ds.cuh"
-#include "qs_pass.cuh"
+#include "qs_internal.cuh"
 
 namespace qs {
 
 namespace {
 
+constexpr int LB = 5;                   // lane bits (contiguous rows of 32 amplitudes)
+constexpr int DK = 12;                  // tile bits
+constexpr int DH = DK - LB;             // high tile bits
+constexpr int DT = 1 << DK;             // amplitudes per tile
+constexpr int DTHREADS = 256;
+constexpr int DMAX_OPS = 80;            // ops per pass
+constexpr int DMINBLOCKS = 3;
+
+enum DsType : uint8_t { D_GEN = 0, D_REAL = 1, D_HB = 2, D_X = 3, D_DIAG = 4 };
+
+// One op (96 bytes).
+struct alignas(16) SOp {
+    uint8_t type;       // DsType
+    uint8_t tbit;       // tile-local target bit; D_DIAG with the target outside the tile: 0xff
+    uint8_t one;        // D_DIAG: 1 d0 == 1 (only target-1 amplitudes change), 2 d1 == 1, 0 neither
+    uint8_t obit;       // D_DIAG with the target outside the tile: its index bit
+    uint32_t tmask, tval;   // control condition over the tile-local (logical) index
+    uint32_t pad;
+    uint64_t omask, oval;   // control condition over the index bits outside the tile
+    float c[16];        // u00, u01, u10, u11 as (re_h, re_l, im_h, im_l); D_DIAG: d0, d1
+};
+static_assert(sizeof(SOp) == 96, "SOp layout");
+
+struct DsPass {
+    const SOp *ops;
+    uint64_t tiles;
+    int32_t nops;
+    float scale_h, scale_l;     // folded Hadamard factor
+    int32_t pad;
+    uint8_t tile_pos[DK];       // ascending; the first LB are 0 .. LB-1
+};
+
 using ds::camp;
 using ds::ccst;
 
-struct DMat {
-    ccst u00, u01, u10, u11;
-};
+__device__ __forceinline__ ccst cst(const float *c) { return {c[0], c[1], c[2], c[3]}; }
+__device__ __forceinline__ camp ld(const float4 &f) { return {f.x, f.y, f.z, f.w}; }
+__device__ __forceinline__ float4 st(const camp &a) { return make_float4(a.rh, a.rl, a.ih, a.il); }
 
-// Matrix of an op: high parts in c[0..3], low parts in c[4..7].
-__device__ __forceinline__ DMat load_dmat(const POp &op) {
-    const float4 *q = reinterpret_cast<const float4 *>(op.c);
-    const float4 h0 = q[0], h1 = q[1], l0 = q[2], l1 = q[3];
-    DMat m;
-    m.u00 = {h0.x, l0.x, h0.y, l0.y};
-    m.u01 = {h0.z, l0.z, h0.w, l0.w};
-    m.u10 = {h1.x, l1.x, h1.y, l1.y};
-    m.u11 = {h1.z, l1.z, h1.w, l1.w};
-    return m;
+// a*x + b*y with real a, b (double-single): each output component is a
+// two-term dot product.
+__device__ __forceinline__ camp rmad2(const ccst &a, const camp &x, const ccst &b, const camp &y) {
+    camp o;
+    ds::dot2(a.rh, a.rl, x.rh, x.rl, b.rh, b.rl, y.rh, y.rl, o.rh, o.rl);
+    ds::dot2(a.rh, a.rl, x.ih, x.il, b.rh, b.rl, y.ih, y.il, o.ih, o.il);
+    return o;
 }
 
-__device__ __forceinline__ camp csel(bool p, const camp &a, const camp &b) {
-    return {p ? a.rh : b.rh, p ? a.rl : b.rl, p ? a.ih : b.ih, p ? a.il : b.il};
+// logical index of pair p with a zero inserted at bit t
+__device__ __forceinline__ uint32_t pair_index(uint32_t p, int t) {
+    return ((p >> t) << (t + 1)) | (p & ((1u << t) - 1u));
 }
 
-__device__ __forceinline__ camp cshfl(const camp &a, int m) {
-    return {__shfl_xor_sync(0xffffffffu, a.rh, m), __shfl_xor_sync(0xffffffffu, a.rl, m),
-            __shfl_xor_sync(0xffffffffu, a.ih, m), __shfl_xor_sync(0xffffffffu, a.il, m)};
-}
-
-__device__ __forceinline__ bool is_one(const ccst &d) { return d.rh == 1.f && d.rl == 0.f && d.ih == 0.f && d.il == 0.f; }
-
-// General 2x2 on register slot T (matrix roles swapped where the slot is
-// deferred-exchanged); with PRED only the pairs whose register bits meet the
-// control condition change.
-template <int T, bool PRED, int NA>
-__device__ __forceinline__ void d_gen(camp (&v)[NA], DMat m, uint32_t xm, int rm, int rv) {
-    if ((xm >> T) & 1) {
-        ccst t = m.u00; m.u00 = m.u11; m.u11 = t;
-        t = m.u01; m.u01 = m.u10; m.u10 = t;
-    }
-#pragma unroll
-    for (int j = 0; j < NA; ++j) {
-        if ((j >> T) & 1) continue;
-        const int j1 = j | (1 << T);
-        const camp x = v[j], y = v[j1];
-        const camp nx = ds::cmad2(m.u00, x, m.u01, y), ny = ds::cmad2(m.u10, x, m.u11, y);
-        if (PRED) {
-            const bool p = lpred(j, xm, rm, rv);
-            v[j] = csel(p, nx, x);
-            v[j1] = csel(p, ny, y);
-        } else {
-            v[j] = nx;
-            v[j1] = ny;
-        }
-    }
-}
-
-template <int T, int NA>
-__device__ __forceinline__ void d_xdata(camp (&v)[NA], uint32_t xm, int rm, int rv, bool ok) {
-#pragma unroll
-    for (int j = 0; j < NA; ++j) {
-        if ((j >> T) & 1) continue;
-        const int j1 = j | (1 << T);
-        const bool p = ok && lpred(j, xm, rm, rv);
-        const camp x = v[j], y = v[j1];
-        v[j] = csel(p, y, x);
-        v[j1] = csel(p, x, y);
-    }
-}
-
-template <int T, int NA>
-__device__ __forceinline__ void d_hb(camp (&v)[NA], uint32_t xm) {
-    const bool sw = (xm >> T) & 1;
-#pragma unroll
-    for (int j = 0; j < NA; ++j) {
-        if ((j >> T) & 1) continue;
-        const int j1 = j | (1 << T);
-        camp x = v[j], y = v[j1];
-        ds::butterfly(x, y);   // x = sum, y = difference
-        const camp nd = {-y.rh, -y.rl, -y.ih, -y.il};
-        v[j] = sw ? nd : x;
-        v[j1] = sw ? x : y;
-    }
-}
-
-template <int T, int NA>
-__device__ __forceinline__ void d_diag(camp (&v)[NA], const ccst &d0, const ccst &d1, uint32_t xm, int rm, int rv) {
-    const bool id0 = is_one(d0), id1 = is_one(d1);
-#pragma unroll
-    for (int j = 0; j < NA; ++j) {
-        const uint32_t l = uint32_t(j) ^ xm;
-        const bool hi = (l >> T) & 1;
-        if ((hi ? id1 : id0) || (l & uint32_t(rm)) != uint32_t(rv)) continue;
-        v[j] = ds::cmul(hi ? d1 : d0, v[j]);
-    }
-}
-
-template <int T, int NA>
-__device__ __forceinline__ void d_reg_op(camp (&v)[NA], int cls, uint32_t &xm, bool ok, int rm, int rv, bool lanectl,
-                                         const POp &op) {
-    if (cls == GC_X) {
-        if (rm == 0 && !lanectl) { xm ^= ok ? (1u << T) : 0u; return; }
-        d_xdata<T, NA>(v, xm, rm, rv, ok);
-        return;
-    }
-    if (!ok) return;
-    if (cls == GC_HB) { d_hb<T, NA>(v, xm); return; }
-    const DMat m = load_dmat(op);
-    if (rm) d_gen<T, true, NA>(v, m, xm, rm, rv);
-    else d_gen<T, false, NA>(v, m, xm, rm, rv);
-}
-
-constexpr int RB = RB64;
-constexpr int NA = 1 << RB;
-
-__global__ void __launch_bounds__(32 << WB64, DS_MINBLOCKS) k_fused_ds(double2 *__restrict__ a,
-                                                                    const __grid_constant__ PassC64 P) {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    const int K = P.K, WB = P.WB, nops = P.nops;
-    float4 *sm = reinterpret_cast<float4 *>(smraw);
-    POp *sops = reinterpret_cast<POp *>(smraw + (P.has_xpose ? (size_t(16) << K) : 0));
+__global__ void __launch_bounds__(DTHREADS, DMINBLOCKS) k_fused_ds(double2 *__restrict__ a,
+                                                                const __grid_constant__ DsPass P) {
+    extern __shared__ __align__(16) float4 smem[];
+    float4 *amp = smem;                                            // DT amplitudes
+    SOp *ops = reinterpret_cast<SOp *>(smem + DT);                 // P.nops ops
+    uint64_t *rowoff = reinterpret_cast<uint64_t *>(ops + P.nops); // 2^DH row offsets
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     {
         const uint4 *src = reinterpret_cast<const uint4 *>(P.ops);
-        uint4 *dst = reinterpret_cast<uint4 *>(sops);
-        const int words = nops * int(sizeof(POp) / 16);
-        for (int k = threadIdx.x; k < words; k += blockDim.x) dst[k] = src[k];
+        uint4 *dst = reinterpret_cast<uint4 *>(ops);
+        for (int k = tid; k < P.nops * int(sizeof(SOp) / 16); k += DTHREADS) dst[k] = src[k];
+        for (int r = tid; r < (1 << DH); r += DTHREADS) {
+            uint64_t o = 0;
+            for (int h = 0; h < DH; ++h)
+                if ((r >> h) & 1) o |= uint64_t(1) << P.tile_pos[LB + h];
+            rowoff[r] = o;
+        }
         __syncthreads();
     }
-    const uint32_t tl = threadIdx.x;
-    const uint32_t lane = tl & 31u, warp = tl >> 5;
-    const int stride = 32 << WB;
-    uint64_t ld_t = lane, st_t = lane;
-#pragma unroll
-    for (int w = 0; w < WB64; ++w)
-        if ((warp >> w) & 1) { ld_t += P.ld_warp[w]; st_t += P.st_warp[w]; }
-
     for (uint64_t tile = blockIdx.x; tile < P.tiles; tile += gridDim.x) {
         uint64_t base = tile;
-        for (int k = 0; k < K; ++k) {
+        for (int k = 0; k < DK; ++k) {
             const uint64_t low = (uint64_t(1) << P.tile_pos[k]) - 1;
             base = ((base & ~low) << 1) | (base & low);
         }
-        uint32_t xm = 0;
-        camp v[NA];
-        {
-            const double2 *src = a + (base | ld_t);
-#pragma unroll
-            for (int j = 0; j < NA; ++j) {
-                const double2 d = src[P.ld_reg[j]];
-                v[j] = ds::load(d.x, d.y);
-            }
+        // load: warp w reads rows w, w + 8, ... (512 contiguous bytes each)
+#pragma unroll 4
+        for (int r = warp; r < (1 << DH); r += DTHREADS / 32) {
+            const double2 d = a[base | rowoff[r] | uint64_t(lane)];
+            amp[(r << LB) | lane] = st(ds::load(d.x, d.y));
         }
-        for (int k = 0; k < nops; ++k) {
-            const POp &op = sops[k];
-            const uint4 *q = reinterpret_cast<const uint4 *>(&op);
-            const uint4 hd = q[0];
-            const int fast = int((hd.y >> 16) & 0xff);
-            if (fast) {
-                const int tp = hd.x >> 24;
-                if (fast == 2) {
-                    const uint4 oc = q[1];
-                    const uint64_t omask = uint64_t(oc.x) | (uint64_t(oc.y) << 32);
-                    const uint64_t oval = uint64_t(oc.z) | (uint64_t(oc.w) << 32);
-                    const bool ok = ((tl & (hd.w & 0xffff)) == (hd.w >> 16)) && ((base & omask) == oval);
-                    xm ^= ok ? (1u << tp) : 0u;
-                    continue;
-                }
-                const DMat m = load_dmat(op);
-                if (fast == 1) {
-                    if (tp == 0) d_gen<0, false, NA>(v, m, xm, 0, 0);
-                    else if (tp == 1) d_gen<1, false, NA>(v, m, xm, 0, 0);
-                    else if (tp == 2) d_gen<2, false, NA>(v, m, xm, 0, 0);
-                    else if (tp == 3) d_gen<3, false, NA>(v, m, xm, 0, 0);
-                    else d_gen<(RB > 4 ? 4 : 0), false, NA>(v, m, xm, 0, 0);
-                } else {
-                    const int msk = 1 << tp;
-                    const bool hi = (lane >> tp) & 1;
-                    const ccst cs = hi ? m.u11 : m.u00, co = hi ? m.u10 : m.u01;
-#pragma unroll
-                    for (int j = 0; j < NA; ++j) {
-                        const camp o = cshfl(v[j], msk);
-                        v[j] = ds::cmad2(cs, v[j], co, o);
-                    }
-                }
+        __syncthreads();
+        uint32_t xm = 0;   // logical index i sits at amp[i ^ xm]
+        for (int k = 0; k < P.nops; ++k) {
+            const SOp &o = ops[k];
+            if ((base & o.omask) != o.oval) continue;   // the same for the whole tile
+            const int type = o.type;
+            const uint32_t tm = o.tmask, tv = o.tval;
+            if (type == D_X && tm == 0) {                // relabel, no data moves
+                xm ^= 1u << o.tbit;
                 continue;
             }
-            const uint4 oc = q[1];
-            const int type = hd.x & 0xff, cls = (hd.x >> 8) & 0xff, tsel = (hd.x >> 16) & 0xff,
-                      tpos = hd.x >> 24;
-            const int rm = hd.y & 0xff, rv = (hd.y >> 8) & 0xff;
-            const uint32_t tm = hd.w & 0xffff, tv = hd.w >> 16;
-            if (type == OP_XPOSE) {
-                const uint32_t cw = (xm * uint32_t(stride)) | tl;
-#pragma unroll
-                for (int j = 0; j < NA; ++j) {
-                    const camp &x = v[j];
-                    sm[uint32_t(j * stride) ^ cw] = make_float4(x.rh, x.rl, x.ih, x.il);
-                }
-                const uint4 *rt = reinterpret_cast<const uint4 *>(op.c);
-                uint32_t rd[16];
-#pragma unroll
-                for (int w4 = 0; w4 < 4; ++w4) {
-                    const uint4 t4 = rt[w4];
-                    rd[4 * w4] = t4.x; rd[4 * w4 + 1] = t4.y; rd[4 * w4 + 2] = t4.z; rd[4 * w4 + 3] = t4.w;
-                }
-                const uint4 ow4 = rt[4];
-                uint32_t cth = lane;
-#pragma unroll
-                for (int w = 0; w < WB64; ++w)
-                    if (w < WB && ((warp >> w) & 1)) cth |= 1u << ((ow4.x >> (8 * w)) & 0xff);
-                __syncthreads();
-                xm = 0;
-#pragma unroll
-                for (int j = 0; j < NA; ++j) {
-                    const float4 f = sm[((rd[j >> 1] >> (16 * (j & 1))) & 0xffff) ^ cth];
-                    v[j] = {f.x, f.y, f.z, f.w};
-                }
-                __syncthreads();
-                continue;
-            }
-            const uint64_t omask = uint64_t(oc.x) | (uint64_t(oc.y) << 32);
-            const uint64_t oval = uint64_t(oc.z) | (uint64_t(oc.w) << 32);
-            const bool ok = ((tl & tm) == tv) && ((base & omask) == oval);
-            if (type == OP_REG) {
-                const bool lc = (tm & 31u) != 0;
-                if (tpos == 0) d_reg_op<0, NA>(v, cls, xm, ok, rm, rv, lc, op);
-                else if (tpos == 1) d_reg_op<1, NA>(v, cls, xm, ok, rm, rv, lc, op);
-                else if (tpos == 2) d_reg_op<2, NA>(v, cls, xm, ok, rm, rv, lc, op);
-                else if (tpos == 3) d_reg_op<3, NA>(v, cls, xm, ok, rm, rv, lc, op);
-                else d_reg_op<(RB > 4 ? 4 : 0), NA>(v, cls, xm, ok, rm, rv, lc, op);
-            } else if (type == OP_LANE) {
-                const int msk = 1 << tpos;
-                const bool hi = (lane >> tpos) & 1;
-                if (cls == GC_HB) {
-#pragma unroll
-                    for (int j = 0; j < NA; ++j) {
-                        const camp o = cshfl(v[j], msk);
-                        // low lane: v + o; high lane: o - v
-                        camp s = hi ? o : v[j], t = hi ? v[j] : o;
-                        float h, l;
-                        ds::add2(s.rh, s.rl, hi ? -t.rh : t.rh, hi ? -t.rl : t.rl, h, l);
-                        camp r;
-                        r.rh = h; r.rl = l;
-                        ds::add2(s.ih, s.il, hi ? -t.ih : t.ih, hi ? -t.il : t.il, h, l);
-                        r.ih = h; r.il = l;
-                        v[j] = r;
-                    }
-                } else if (cls == GC_X) {
-#pragma unroll
-                    for (int j = 0; j < NA; ++j) {
-                        const camp o = cshfl(v[j], msk);
-                        if (ok && lpred(j, xm, rm, rv)) v[j] = o;
+            if (type == D_DIAG) {
+                const ccst d0 = cst(o.c), d1 = cst(o.c + 4);
+                if (o.tbit == 0xff) {
+                    const ccst d = ((base >> o.obit) & 1) ? d1 : d0;
+                    if (!(d.rh == 1.f && d.rl == 0.f && d.ih == 0.f && d.il == 0.f)) {
+                        for (uint32_t i = tid; i < uint32_t(DT); i += DTHREADS)
+                            if ((i & tm) == tv) amp[i ^ xm] = st(ds::cmul(d, ld(amp[i ^ xm])));
                     }
                 } else {
-                    const DMat m = load_dmat(op);
-                    const ccst cs = hi ? m.u11 : m.u00, co = hi ? m.u10 : m.u01;
-#pragma unroll
-                    for (int j = 0; j < NA; ++j) {
-                        const camp o = cshfl(v[j], msk);
-                        if (ok && lpred(j, xm, rm, rv)) v[j] = ds::cmad2(cs, v[j], co, o);
+                    const int t = o.tbit;
+                    const int one = o.one;
+                    for (uint32_t p = tid; p < uint32_t(DT / 2); p += DTHREADS) {
+                        const uint32_t i0 = pair_index(p, t), i1 = i0 | (1u << t);
+                        if (one != 1 && (i0 & tm) == tv) amp[i0 ^ xm] = st(ds::cmul(d0, ld(amp[i0 ^ xm])));
+                        if (one != 2 && (i1 & tm) == tv) amp[i1 ^ xm] = st(ds::cmul(d1, ld(amp[i1 ^ xm])));
                     }
                 }
-            } else {  // OP_DIAG
-                if (!ok) continue;
-                const DMat m = load_dmat(op);
-                const ccst d0 = m.u00, d1 = m.u01;
-                if (tsel == 0) {
-                    if (tpos == 0) d_diag<0, NA>(v, d0, d1, xm, rm, rv);
-                    else if (tpos == 1) d_diag<1, NA>(v, d0, d1, xm, rm, rv);
-                    else if (tpos == 2) d_diag<2, NA>(v, d0, d1, xm, rm, rv);
-                    else if (tpos == 3) d_diag<3, NA>(v, d0, d1, xm, rm, rv);
-                    else d_diag<(RB > 4 ? 4 : 0), NA>(v, d0, d1, xm, rm, rv);
-                } else {
-                    const uint64_t word = tsel == 1 ? uint64_t(tl) : base;
-                    const ccst d = ((word >> tpos) & 1) ? d1 : d0;
-                    if (is_one(d)) continue;   // this thread's entry is exactly 1
-#pragma unroll
-                    for (int j = 0; j < NA; ++j)
-                        if (lpred(j, xm, rm, rv)) v[j] = ds::cmul(d, v[j]);
+            } else {
+                const int t = o.tbit;
+                const ccst u00 = cst(o.c), u01 = cst(o.c + 4), u10 = cst(o.c + 8), u11 = cst(o.c + 12);
+                for (uint32_t p = tid; p < uint32_t(DT / 2); p += DTHREADS) {
+                    const uint32_t i0 = pair_index(p, t), i1 = i0 | (1u << t);
+                    if ((i0 & tm) != tv) continue;
+                    const uint32_t q0 = i0 ^ xm, q1 = i1 ^ xm;
+                    camp x = ld(amp[q0]), y = ld(amp[q1]);
+                    if (type == D_X) {
+                        amp[q0] = st(y);
+                        amp[q1] = st(x);
+                        continue;
+                    }
+                    if (type == D_HB) {
+                        ds::butterfly(x, y);
+                    } else if (type == D_REAL) {
+                        const camp nx = rmad2(u00, x, u01, y), ny = rmad2(u10, x, u11, y);
+                        x = nx;
+                        y = ny;
+                    } else {
+                        const camp nx = ds::cmad2(u00, x, u01, y), ny = ds::cmad2(u10, x, u11, y);
+                        x = nx;
+                        y = ny;
+                    }
+                    amp[q0] = st(x);
+                    amp[q1] = st(y);
                 }
             }
+            __syncthreads();
         }
-        if (P.scale != 1.f || P.scale_lo != 0.f) {
-#pragma unroll
-            for (int j = 0; j < NA; ++j) {
-                camp &x = v[j];
-                ds::mul1(x.rh, x.rl, P.scale, P.scale_lo, x.rh, x.rl);
-                ds::mul1(x.ih, x.il, P.scale, P.scale_lo, x.ih, x.il);
+        // store (with the folded Hadamard factor)
+        const bool scale = P.scale_h != 1.f || P.scale_l != 0.f;
+#pragma unroll 4
+        for (int r = warp; r < (1 << DH); r += DTHREADS / 32) {
+            camp x = ld(amp[((uint32_t(r) << LB) | uint32_t(lane)) ^ xm]);
+            if (scale) {
+                ds::mul1(x.rh, x.rl, P.scale_h, P.scale_l, x.rh, x.rl);
+                ds::mul1(x.ih, x.il, P.scale_h, P.scale_l, x.ih, x.il);
             }
+            a[base | rowoff[r] | uint64_t(lane)] = make_double2(ds::join(x.rh, x.rl), ds::join(x.ih, x.il));
         }
-        double2 *dst = a + (base | st_t);
-        uint64_t xg = 0;
-#pragma unroll
-        for (int r = 0; r < RB; ++r)
-            if ((xm >> r) & 1) xg |= P.st_reg[1 << r];
-#pragma unroll
-        for (int j = 0; j < NA; ++j) {
-            const camp &x = v[j];
-            dst[P.st_reg[j] ^ xg] = make_double2(ds::join(x.rh, x.rl), ds::join(x.ih, x.il));
-        }
+        __syncthreads();
     }
 }
 
+size_t ds_smem(int nops) { return size_t(DT) * 16 + size_t(nops) * sizeof(SOp) + (size_t(8) << DH); }
+
+bool diag_cls(int cls) { return cls == GC_DIAG || cls == GC_PHASE; }
+
 }  // namespace
 
-cudaError_t launch_fused_ds(unsigned grid, unsigned block, size_t smem, cudaStream_t st, double2 *a,
-                            const PassC64 &D) {
-    k_fused_ds<<<grid, block, smem, st>>>(a, D);
-    return cudaGetLastError();
+struct DsPlan {
+    int n = 0;
+    std::vector<DsPass> passes;
+    std::vector<std::vector<SOp>> tables;
+    std::vector<std::vector<int>> order;    // per pass: indices into ex, in execution order
+    std::vector<HostOp> ex;                 // the planned ops (SWAPs as three C-NOTs)
+    void *dev = nullptr;
+    bool temp = false;
+    cudaStream_t free_stream = nullptr;
+    int grid = 0;
+    ~DsPlan() {
+        if (dev) {
+            if (temp) cudaFreeAsync(dev, free_stream);
+            else cudaFree(dev);
+        }
+    }
+};
+
+qs_status ds_plan_build(int n, const std::vector<HostOp> &ops, int max_ops, bool temp, DsPlan **out) {
+    if (n < DK) return fail(QS_EUNSUPPORTED, "double-single passes need n >= 12");
+    DsPlan *P = new DsPlan();
+    P->n = n;
+    P->temp = temp;
+    expand_swap_ops(ops, P->ex);
+    for (size_t i = 0; i < P->ex.size(); ++i) P->ex[i].step = int32_t(i);
+    max_ops = std::max(4, std::min(max_ops > 0 ? max_ops : 2 * DMAX_OPS, 2 * DMAX_OPS));
+    for (const PassGroup &gp : group_passes(n, DH, max_ops, P->ex)) {
+        DsPass D;
+        std::memset(&D, 0, sizeof(D));
+        for (int k = 0; k < LB; ++k) D.tile_pos[k] = uint8_t(k);
+        int local[64];
+        for (int b = 0; b < 64; ++b) local[b] = -1;
+        for (int k = 0; k < LB; ++k) local[k] = k;
+        for (int h = 0; h < DH; ++h) {
+            D.tile_pos[LB + h] = uint8_t(gp.high[size_t(h)]);
+            local[gp.high[size_t(h)]] = LB + h;
+        }
+        std::vector<SOp> tab;
+        int n_hb = 0;
+        for (int idx : gp.idx) {
+            const HostOp &o = P->ex[size_t(idx)];
+            SOp s;
+            std::memset(&s, 0, sizeof(s));
+            for (int b = 0; b < n; ++b) {
+                if (!((o.cmask >> b) & 1)) continue;
+                const uint64_t v = (o.cval >> b) & 1;
+                if (local[b] >= 0) {
+                    s.tmask |= 1u << local[b];
+                    s.tval |= uint32_t(v) << local[b];
+                } else {
+                    s.omask |= uint64_t(1) << b;
+                    s.oval |= v << b;
+                }
+            }
+            auto put = [&](int e, double re, double im) {
+                ds::split_const(re, s.c[4 * e], s.c[4 * e + 1]);
+                ds::split_const(im, s.c[4 * e + 2], s.c[4 * e + 3]);
+            };
+            if (diag_cls(o.cls)) {
+                s.type = D_DIAG;
+                double d0r = o.u[0], d0i = o.u[1], d1r = o.u[6], d1i = o.u[7];
+                if (o.cls == GC_PHASE) {
+                    if (o.phase_on) { d0r = 1; d0i = 0; } else { d1r = 1; d1i = 0; }
+                }
+                put(0, d0r, d0i);
+                put(1, d1r, d1i);
+                s.one = uint8_t((d0r == 1 && d0i == 0) ? 1 : (d1r == 1 && d1i == 0) ? 2 : 0);
+                if (local[o.bit] >= 0) s.tbit = uint8_t(local[o.bit]);
+                else { s.tbit = 0xff; s.obit = uint8_t(o.bit); }
+            } else {
+                if (local[o.bit] < 0) { delete P; return fail(QS_EUNSUPPORTED, "planner: target outside the tile"); }
+                s.tbit = uint8_t(local[o.bit]);
+                const bool real = o.u[1] == 0 && o.u[3] == 0 && o.u[5] == 0 && o.u[7] == 0;
+                if (o.cls == GC_X) s.type = D_X;
+                else if (o.kind == QS_GATE_H && o.cmask == 0) { s.type = D_HB; ++n_hb; }
+                else s.type = real ? D_REAL : D_GEN;
+                for (int e = 0; e < 4; ++e) put(e, o.u[2 * e], o.u[2 * e + 1]);
+            }
+            tab.push_back(s);
+        }
+        if (int(tab.size()) > DMAX_OPS) { delete P; return fail(QS_EUNSUPPORTED, "planner: pass too large"); }
+        double sc = std::ldexp(1.0, -(n_hb / 2));
+        if (n_hb & 1) sc *= 1.0 / std::sqrt(2.0);
+        ds::split_const(sc, D.scale_h, D.scale_l);
+        D.nops = int32_t(tab.size());
+        D.tiles = uint64_t(1) << (n - DK);
+        P->passes.push_back(D);
+        P->tables.push_back(std::move(tab));
+        P->order.push_back(gp.idx);
+    }
+    *out = P;
+    return QS_OK;
 }
 
-const void *fused_ds_kernel() { return reinterpret_cast<const void *>(&k_fused_ds); }
+// Uploads the op tables on first use and sizes the grid.
+static cudaError_t ds_ensure_device(DsPlan *P, cudaStream_t st) {
+    if (P->dev || P->passes.empty()) return cudaSuccess;
+    std::vector<SOp> flat;
+    std::vector<size_t> offs;
+    for (auto &t : P->tables) {
+        offs.push_back(flat.size());
+        flat.insert(flat.end(), t.begin(), t.end());
+    }
+    const size_t bytes = std::max<size_t>(1, flat.size()) * sizeof(SOp);
+    cudaError_t e;
+    if (P->temp) {
+        e = cudaMallocAsync(&P->dev, bytes, st);
+        if (e != cudaSuccess) return e;
+        P->free_stream = st;
+        e = cudaMemcpyAsync(P->dev, flat.data(), flat.size() * sizeof(SOp), cudaMemcpyHostToDevice, st);
+    } else {
+        e = cudaMalloc(&P->dev, bytes);
+        if (e != cudaSuccess) return e;
+        e = cudaMemcpy(P->dev, flat.data(), flat.size() * sizeof(SOp), cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) return e;
+    for (size_t k = 0; k < P->passes.size(); ++k) P->passes[k].ops = static_cast<const SOp *>(P->dev) + offs[k];
+    static int grid_cache[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int &g = grid_cache[dev & 63];
+    if (g == 0) {
+        int sms = 0, per_sm = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const size_t smax = ds_smem(DMAX_OPS);
+        e = cudaFuncSetAttribute(k_fused_ds, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smax));
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_ds, DTHREADS, smax);
+        if (e != cudaSuccess) return e;
+        g = std::max(1, sms * std::max(1, per_sm));
+    }
+    P->grid = g;
+    return cudaSuccess;
+}
+
+cudaError_t ds_plan_run(DsPlan *P, double2 *state, cudaStream_t st, Plan *timing) {
+    cudaError_t e = ds_ensure_device(P, st);
+    if (e != cudaSuccess) return e;
+    for (const DsPass &D : P->passes) {
+        const uint64_t grid = std::min<uint64_t>(D.tiles, uint64_t(P->grid));
+        e = plan_mark(timing, st, false);
+        if (e != cudaSuccess) return e;
+        k_fused_ds<<<unsigned(grid), DTHREADS, ds_smem(D.nops), st>>>(state, D);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        e = plan_mark(timing, st, true);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+int64_t ds_plan_launches(const DsPlan *P) { return int64_t(P->passes.size()); }
+
+std::string ds_plan_describe(const DsPlan *P) {
+    std::string out;
+    char line[640];
+    for (size_t k = 0; k < P->passes.size(); ++k) {
+        const DsPass &D = P->passes[k];
+        int cnt[5] = {0, 0, 0, 0, 0}, xdef = 0;
+        for (const SOp &s : P->tables[k]) {
+            if (s.type == D_X && s.tmask == 0) ++xdef;
+            else ++cnt[s.type];
+        }
+        std::string bits;
+        for (int i = 0; i < DK; ++i) bits += (i ? "," : "") + std::to_string(int(D.tile_pos[i]));
+        std::snprintf(line, sizeof(line),
+                      "pass %zu: K=%d double-single gen=%d real=%d hb=%d x_deferred=%d x_moved=%d diag=%d bits=[%s]\n",
+                      k, DK, cnt[D_GEN], cnt[D_REAL], cnt[D_HB], xdef, cnt[D_X], cnt[D_DIAG], bits.c_str());
+        out += line;
+        out += "  order=";
+        for (size_t i = 0; i < P->order[k].size(); ++i) out += (i ? "," : "") + std::to_string(P->order[k][i]);
+        out += "\n";
+    }
+    for (size_t i = 0; i < P->ex.size(); ++i) {
+        const HostOp &o = P->ex[i];
+        std::snprintf(line, sizeof(line),
+                      "op %zu bit=%d cmask=%llx cval=%llx u=%.17g,%.17g,%.17g,%.17g,%.17g,%.17g,%.17g,%.17g\n", i,
+                      int(o.bit), (unsigned long long)o.cmask, (unsigned long long)o.cval, o.u[0], o.u[1], o.u[2],
+                      o.u[3], o.u[4], o.u[5], o.u[6], o.u[7]);
+        out += line;
+    }
+    return out;
+}
+
+void ds_plan_destroy(DsPlan *P) { delete P; }
 
 }  // namespace qs

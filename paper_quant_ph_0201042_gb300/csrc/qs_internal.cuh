@@ -171,5 +171,19 @@ struct PassGroup {
 };
 std::vector<PassGroup> group_passes(int n, int H, int max_ops, const std::vector<HostOp> &ops);
 qs_dtype plan_dtype(const Plan *p);
+// A SWAP (with optional controls C) as C-NOTs CX(b->a), CX(C + a -> b), CX(b->a);
+// identity ops dropped.
+void expand_swap_ops(const std::vector<HostOp> &in, std::vector<HostOp> &out);
+// Records a timing event around a launch when the plan's per-launch timing
+// is on (qs_plan_set_timing); a no-op otherwise or for a NULL plan.
+cudaError_t plan_mark(Plan *p, cudaStream_t st, bool end);
+
+// Double-single fused passes over a complex128 state (qs_fused_ds.cu).
+struct DsPlan;
+qs_status ds_plan_build(int n, const std::vector<HostOp> &ops, int max_ops, bool temp, DsPlan **out);
+cudaError_t ds_plan_run(DsPlan *p, double2 *state, cudaStream_t st, Plan *timing);
+int64_t ds_plan_launches(const DsPlan *p);
+std::string ds_plan_describe(const DsPlan *p);
+void ds_plan_destroy(DsPlan *p);
 
 }  // namespace qs
