@@ -1,13 +1,16 @@
 """Throughput benchmark of the random-circuit workload: n = 30 qubits, 40 layers
 of Haar-random SU(2) gates on every qubit followed by C-NOTs on 15 random
-disjoint pairs (1800 gates), complex64 state (8 GiB) by default.
+disjoint pairs (1800 gates), complex128 state (16 GiB, the paper's double
+precision) by default.
 
 One step = one simulation of the whole circuit from |0...0>: qs_init_basis
-followed by the fused circuit plan (every gate of the circuit).  Prints one
-JSON line (see --help).
+followed by the fused circuit plan (every gate of the circuit).  The
+complex128 passes compute in double-single arithmetic (the library's default
+for complex128; --arith f64 selects double-precision instructions).  Prints
+one JSON line (see --help).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--dtype c64|c128]
-                  [--no-fuse] [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--dtype c128|c64]
+                  [--arith default|f64] [--no-fuse] [--impl ours|reference]
 
 --impl reference times the CPU oracle (complex128, plain row-by-row gate
 application) on the host cores, on a bounded sample of the same workload.
@@ -52,9 +55,15 @@ def amp_updates(n, gates):
 
 def workload_config(args, n_ranks):
     n = args.n
+    if args.dtype == "c64":
+        kind = "complex64"
+    elif args.no_fuse or args.arith == "f64":
+        kind = "complex128 (double-precision instructions)"
+    else:
+        kind = "complex128 (double-single arithmetic)"
     return {
         "workload": "random circuit n=%d, %d layers (Haar SU(2) on every qubit + C-NOTs on %d disjoint pairs), %s state"
-                    % (n, LAYERS, n // 2, "complex64" if args.dtype == "c64" else "complex128"),
+                    % (n, LAYERS, n // 2, kind),
         "n_qubits": n, "layers": LAYERS, "gates": LAYERS * (n + n // 2),
         "state_bytes": (8 if args.dtype == "c64" else 16) << n,
         "fused": not args.no_fuse,
@@ -218,6 +227,81 @@ def _time(torch, fn, reps=1):
     return e0.elapsed_time(e1) / reps
 
 
+# FP32 instructions per changed amplitude of the double-single arithmetic of
+# the complex128 fused pass (qs_ds.cuh): a general 2x2 gate makes two
+# four-term dot products per amplitude (re, im) of 43 instructions each (four
+# exact products with their low-order terms, three TwoSums, the low-order
+# sum and a FastTwoSum)
+DS_INSTR_GENERAL = 86
+# DRAM bytes (read + write) of one complex128 double-single pass at n = 26,
+# from one ncu capture of k_fused_ds (2.0866 GB against 2.147 GB algorithmic);
+# a pass moves every amplitude once, so a launch at n scales by 2^(n-26)
+DS_TRAFFIC_N26 = 2.0866e9
+# the same for the complex64 pass k_fused_c64 (1013.5 MB per n = 26 launch)
+C64_TRAFFIC_N26 = 1013.5e6
+
+
+def general_gates(gates):
+    return sum(1 for g in gates if g.kind == "MATRIX")
+
+
+def rooflines(args, n, gates, kern_ms_step, launches_step, sm_mhz, sms, peaks):
+    """Roofline views of the dominant kernel from its per-launch device time.
+    hbm: one read and one write of the state per pass (fused) or of the
+    touched amplitudes per gate (unfused); alu: the arithmetic of the general
+    gates (the C-NOTs move no data in the fused passes)."""
+    amp_bytes = 8 if args.dtype == "c64" else 16
+    hbm_peak, hbm_src = measured_peaks()
+    if args.no_fuse:
+        bytes_step = sum(2 * amp_bytes * (1 << (n - len(g.controls))) for g in gates)
+    else:
+        bytes_step = launches_step * 2 * (amp_bytes << n)
+    t = kern_ms_step / 1e3
+    views = {"hbm": {"achieved": bytes_step / t / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": bytes_step / t / 1e9 / hbm_peak, "peak_source": hbm_src + " copy bandwidth"}}
+    ngen = general_gates(gates)
+    issue_peak = sms * 128 * sm_mhz * 1e6          # FP32 lanes x SM clock (instructions/s)
+    fp64_flops = ngen * 16 * (1 << n)              # 8 double multiply-adds per amplitude
+    ds = args.dtype == "c128" and args.arith != "f64" and not args.no_fuse
+    if ds:
+        instr = ngen * DS_INSTR_GENERAL * (1 << n)
+        views["alu"] = {"achieved": instr / t / 1e12, "peak": issue_peak / 1e12, "unit": "T FP32 instr/s",
+                        "frac": instr / t / issue_peak,
+                        "peak_source": "%d SMs x 128 FP32 lanes x %.0f MHz (measured SM clock)" % (sms, sm_mhz),
+                        "peak_measured_ffma": peaks["f32"] / 1e12,
+                        "work": "%d FP32 instructions per amplitude per general gate (double-single)"
+                                % DS_INSTR_GENERAL}
+        views["fp64_equivalent"] = {"achieved": fp64_flops / t / 1e12, "unit": "TFLOP/s (FP64 flops of the gates)",
+                                    "fp64_pipe_peak_measured": 2 * peaks["f64"] / 1e12,
+                                    "ratio_to_fp64_pipe": fp64_flops / t / (2 * peaks["f64"])}
+    elif args.dtype == "c128":
+        views["alu"] = {"achieved": fp64_flops / t / 1e12, "peak": 2 * peaks["f64"] / 1e12, "unit": "TFLOP/s",
+                        "frac": fp64_flops / t / (2 * peaks["f64"]),
+                        "peak_source": "measured FP64 FMA rate (qs_alu_peak) x 2 flops"}
+    else:
+        flops = ngen * 16 * (1 << n)
+        peak = sms * 128 * 2 * sm_mhz * 1e6
+        views["alu"] = {"achieved": flops / t / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+                        "frac": flops / t / peak,
+                        "peak_source": "%d SMs x 128 FP32 lanes x 2 flops x %.0f MHz (measured SM clock)" % (sms, sm_mhz),
+                        "peak_measured_ffma": 2 * peaks["f32"] / 1e12}
+    t_hbm = bytes_step / (hbm_peak * 1e9)
+    t_alu = views["alu"]["achieved"] * t / views["alu"]["peak"] if "peak" in views["alu"] else 0.0
+    bound = "alu" if t_alu > t_hbm else "hbm"
+    main = views[bound]
+    if args.no_fuse:
+        traffic, kern = None, "k_pair"
+    elif ds:
+        traffic, kern = DS_TRAFFIC_N26 * (1 << (n - 26)), "k_fused_ds"
+    elif args.dtype == "c64":
+        traffic, kern = C64_TRAFFIC_N26 * (1 << (n - 26)), "k_fused_c64"
+    else:
+        traffic, kern = None, "k_fused<double,4>"
+    return {"bound": bound, "achieved": main["achieved"], "peak": main["peak"], "unit": main["unit"],
+            "frac": main["frac"], "traffic": traffic, "traffic_unit": "bytes per launch", "kernel": kern,
+            "peak_source": main["peak_source"], "views": views}
+
+
 def e2e_pipelined(torch, qs, state, n, dtype, garr, n_gates, opts, k, dist, local):
     """k end-to-end steps through the public C ABI, alternating between two
     states on two streams: each step initialises its state, applies the
@@ -274,67 +358,170 @@ def e2e_pipelined(torch, qs, state, n, dtype, garr, n_gates, opts, k, dist, loca
         other.close()
 
 
-def secondary(args, torch, qs, state64):
-    """The other measurements the metric names, each on its own workload:
-    the complex128 state at n = 30 (same circuit), the adjoint gradient
-    against finite differences at n = 26 (25 layers, 1300 angles), and the
-    4096-trajectory noisy batch."""
+def _release(torch):
+    release = getattr(torch._C, "_host_emptyCache", None)
+    if release is not None:
+        release()
+    torch.cuda.empty_cache()
+
+
+def secondary(args, torch, qs, state128, peaks, sms, sm_mhz):
+    """The other measurements the metric and the workloads name, each on its
+    own workload: the complex64 state at n = 30 (same circuit) and its
+    distance to the complex128 result, double-precision instructions against
+    double-single at n = 28, the unfused per-gate path, the FFT QFT, the
+    adjoint gradient against measured finite differences and parameter
+    shifts, the 4096-trajectory batch, and Grover n = 24."""
+    import ctypes
+    from paper_quant_ph_0201042_gb300 import paper
     out = {}
     n = args.n
     gates = W.random_circuit(n, LAYERS, seed=SEED)
     upd = amp_updates(n, gates)
-    # the QFT black box (FFT, Sec. 2.3.2) on the same complex64 register:
-    # 4 transform passes and a bit-reversal pass, each one read + one write
-    if state64 is not None:
-        state64.qft()
-        t = _time(torch, lambda: state64.qft(), reps=3)
-        nbytes = 5 * 2 * (8 << n)
-        out["qft_fft_c64"] = {"workload": "QFT of all %d qubits by the FFT (qs_qft), complex64" % n,
-                              "ms": t, "hbm_gbs_5_passes": nbytes / (t / 1e3) / 1e9,
-                              "frac_of_measured_hbm": nbytes / (t / 1e3) / 1e9 / measured_peaks()[0]}
-    # complex128: one warm-up, one timed step (FP64-ALU bound)
-    if state64 is not None:
-        state64.close()
-    torch.cuda.empty_cache()
-    p128 = qs.Plan(n, "c128", gates)
-    s128 = qs.State(n, "c128")
-    step = lambda: (s128.init_basis(0), p128.execute(s128))
-    step()
-    p128.set_timing(True)
-    p128.timing()
-    ms = _time(torch, step)
-    kms, kn = p128.timing()
-    flops = sum(16 * (1 << n) for g in gates if g.kind == "MATRIX")
-    out["c128"] = {"value": upd / (ms / 1e3), "unit": "amp-updates/s", "ms_per_step": ms,
-                   "passes": p128.launches,
-                   "roofline": {"bound": "alu", "achieved": flops / (kms / 1e3) / 1e12, "peak": 1.25,
-                                "unit": "TFLOP/s", "frac": flops / (kms / 1e3) / 1e12 / 1.25,
-                                "peak_source": "nominal FP64 1.25 TFLOP/s", "kernel": "k_fused<double,4>"}}
-    s128.close()
-    del p128
-    torch.cuda.empty_cache()
-    # adjoint gradient at n = 26 vs finite differences / parameter shift
+    ngen = general_gates(gates)
+    hbm_peak = measured_peaks()[0]
+
+    # complex64 state, same circuit: throughput, roofline, distance to complex128
+    p64 = qs.Plan(n, "c64", gates)
+    s64 = qs.State(n, "c64")
+    step64 = lambda: (s64.init_basis(0), p64.execute(s64))
+    step64()
+    ms64 = _time(torch, step64, reps=3)
+    p64.set_timing(True)
+    p64.timing()
+    step64()
+    kms, kn = p64.timing()
+    p64.set_timing(False)
+    flops = ngen * 16 * (1 << n)
+    fpk = sms * 128 * 2 * sm_mhz * 1e6
+    c64 = {"value": upd / (ms64 / 1e3), "unit": "amp-updates/s", "ms_per_step": ms64, "passes": p64.launches,
+           "roofline": {"bound": "alu", "kernel": "k_fused_c64", "achieved": flops / (kms / 1e3) / 1e12,
+                        "peak": fpk / 1e12, "unit": "TFLOP/s", "frac": flops / (kms / 1e3) / fpk,
+                        "hbm_gbs": kn * 2 * (8 << n) / (kms / 1e3) / 1e9,
+                        "hbm_frac": kn * 2 * (8 << n) / (kms / 1e3) / 1e9 / hbm_peak,
+                        "traffic": C64_TRAFFIC_N26 * (1 << (n - 26))}}
+    if state128 is not None:
+        d = (s64.tensor.to(torch.complex128) - state128.tensor).abs().pow(2).sum().sqrt().item()
+        c64["state_error_vs_c128"] = d
+    out["c64"] = c64
+    s64.close()
+    del p64
+    _release(torch)
+
+    # double-precision instructions against double-single, n = 28 (the n = 30
+    # step with doubles takes about 18 s): time and the distance of the states
+    nd = 28
+    gd = W.random_circuit(nd, LAYERS, seed=SEED)
+    res = {}
+    sts = {}
+    for ar in ("f64", "default"):
+        pl = qs.Plan(nd, "c128", gd, arith=ar)
+        st = qs.State(nd, "c128")
+        run = lambda: (st.init_basis(0), pl.execute(st))
+        run()
+        ms = _time(torch, run)
+        res[ar] = {"ms": ms, "passes": pl.launches, "value": amp_updates(nd, gd) / (ms / 1e3)}
+        sts[ar] = st
+        del pl
+    dd = (sts["f64"].tensor - sts["default"].tensor).abs().pow(2).sum().sqrt().item()
+    out["c128_f64_vs_double_single_n28"] = {
+        "workload": "random circuit n=28, 40 layers, complex128", "f64_instructions": res["f64"],
+        "double_single": res["default"], "speedup": res["f64"]["ms"] / res["default"]["ms"],
+        "fp64_peak_measured_tflops": 2 * peaks["f64"] / 1e12,
+        "f64_fraction_of_fp64_pipe": general_gates(gd) * 16 * (1 << nd) / (res["f64"]["ms"] / 1e3)
+                                     / (2 * peaks["f64"]),
+        "state_distance": dd}
+    for st in sts.values():
+        st.close()
+    _release(torch)
+
+    # unfused per-gate path (one pair sweep per gate), complex128 with double
+    # instructions, on the first two layers of the n = 30 circuit
+    if state128 is not None:
+        pre = gates[:2 * (n + n // 2)]
+        pu = qs.Plan(n, "c128", pre, fuse=False)
+        run = lambda: pu.execute(state128)
+        ms = _time(torch, run)
+        ub = sum(2 * 16 * (1 << (n - len(g.controls))) for g in pre)
+        out["unfused_c128_n30"] = {"gates": len(pre), "ms": ms, "gates_per_s": len(pre) / (ms / 1e3),
+                                   "amp_updates_per_s": amp_updates(n, pre) / (ms / 1e3),
+                                   "hbm_gbs": ub / (ms / 1e3) / 1e9, "hbm_frac": ub / (ms / 1e3) / 1e9 / hbm_peak,
+                                   "note": "first 2 of 40 layers; one launch per gate, double-precision "
+                                           "instructions (FP64-pipe bound on this part)"}
+        del pu
+
+    # the QFT black box (FFT, Sec. 2.3.2), complex64 n = 30: 4 transform
+    # passes and a bit-reversal pass, each one read + one write
+    sq = qs.State(n, "c64").init_basis(12345)
+    sq.qft()
+    t = _time(torch, lambda: sq.qft(), reps=3)
+    nbytes = 5 * 2 * (8 << n)
+    out["qft_fft_c64"] = {"workload": "QFT of all %d qubits by the FFT (qs_qft), complex64" % n, "ms": t,
+                          "hbm_gbs_5_passes": nbytes / (t / 1e3) / 1e9,
+                          "frac_of_measured_hbm": nbytes / (t / 1e3) / 1e9 / hbm_peak}
+    sq.close()
+    _release(torch)
+
+    # adjoint gradient at n = 26 (complex64) against measured finite
+    # differences and parameter shifts on a few angles, and the plain per-step
+    # sweep with double instructions on a complex128 state
     na = 26
     agates, aparams = W.ansatz_circuit(na, 25, seed=2026)
-    work = qs.State(na, "c64")
     pauli = "Z" + "I" * (na - 1)
+    work = qs.State(na, "c64")
     qs.adjoint_grad(work, agates, aparams, pauli=pauli)
-    t_adj = _time(torch, lambda: qs.adjoint_grad(work, agates, aparams, pauli=pauli))
+    t_adj = _time(torch, lambda: qs.adjoint_grad(work, agates, aparams, pauli=pauli), reps=3)
     pf = qs.Plan(na, "c64", agates)
     fwd = lambda: (work.init_basis(0), pf.execute(work), work.expect(pauli))
     fwd()
     t_fwd = _time(torch, fwd, reps=3)
+
+    def energy(prm):
+        gs = [W.Gate(g.kind, g.target, controls=g.controls,
+                     angles=((float(prm[g.param]),) if g.param >= 0 else g.angles), param=g.param)
+              for g in agates]
+        work.init_basis(0).apply_circuit(gs)
+        return work.expect(pauli)
+
+    sample = [0, 333, 777, 1299]
+    t0 = time.perf_counter()
+    for k in sample:                    # central differences, h = 1e-4
+        for sgn in (1, -1):
+            prm = aparams.copy()
+            prm[k] += sgn * 1e-4
+            energy(prm)
+    t_fd = (time.perf_counter() - t0) / len(sample)
+    t0 = time.perf_counter()
+    for k in sample:                    # parameter shift: E(t + pi/2) - E(t - pi/2), over 2
+        for sgn in (1, -1):
+            prm = aparams.copy()
+            prm[k] += sgn * math.pi / 2
+            energy(prm)
+    t_ps = (time.perf_counter() - t0) / len(sample)
     n_par = aparams.size
-    out["adjoint"] = {"workload": "ansatz n=26, 25 layers of RY/RZ + C-NOT ladder, 1300 angles, complex64, <Z_0>",
-                      "adjoint_ms": t_adj, "forward_ms": t_fwd,
-                      "finite_diff_ms_estimate": 2 * n_par * t_fwd,
-                      "speedup_vs_finite_diff": 2 * n_par * t_fwd / t_adj,
-                      "speedup_vs_parameter_shift": 2 * n_par * t_fwd / t_adj,
-                      "note": "finite differences and the parameter-shift rule both take 2 forward passes per "
-                              "angle; their cost is 2 x 1300 x the measured forward time"}
     work.close()
     del pf
-    torch.cuda.empty_cache()
+    _release(torch)
+    w128 = qs.State(na, "c128")
+    t0 = time.perf_counter()
+    qs.adjoint_grad(w128, agates, aparams, pauli=pauli, fuse=False)
+    t_plain = time.perf_counter() - t0
+    w128.close()
+    _release(torch)
+    out["adjoint"] = {
+        "workload": "ansatz n=26, 25 layers of RY/RZ + C-NOT ladder, 1300 angles, complex64, <Z_0>",
+        "adjoint_ms": t_adj, "forward_ms": t_fwd, "adjoint_over_forward": t_adj / t_fwd,
+        "finite_diff_ms_per_angle_measured": t_fd * 1e3, "finite_diff_ms_all_angles": t_fd * 1e3 * n_par,
+        "parameter_shift_ms_per_angle_measured": t_ps * 1e3, "parameter_shift_ms_all_angles": t_ps * 1e3 * n_par,
+        "speedup_vs_finite_diff": t_fd * 1e3 * n_par / t_adj,
+        "speedup_vs_parameter_shift": t_ps * 1e3 * n_par / t_adj,
+        "sample": "finite differences and parameter shifts timed end to end (circuit from host gates, forward "
+                  "passes, <Z_0>) on angles %s, 2 runs each, then x %d angles" % (sample, n_par),
+        "plain_fp64_per_step_sweep_ms": t_plain * 1e3,
+        "speedup_vs_plain_fp64": t_plain * 1e3 / t_adj,
+        "plain_fp64_note": "qs_adjoint_grad_ex with no_fusion = 1 on a complex128 state: one sweep of both "
+                           "vectors per step, double-precision instructions"}
+
     # batched noisy trajectories
     batch = W.trajectory_batch(4096, ((12, 2), (16, 1), (20, 1)), (12, 16), seed=31337)
     groups = qs.batch_groups(batch)
@@ -342,40 +529,56 @@ def secondary(args, torch, qs, state64):
     t0 = time.perf_counter()
     met, _ = qs.run_trajectories(groups, 1e-3, 1e-2, 7, dtype="c64", with_stats=False)
     dt = time.perf_counter() - t0
-    hist, edges = np.histogram(met, bins=10, range=(0.0, 1.0))
-    tupd = 0
+    hist, _ = np.histogram(met, bins=10, range=(0.0, 1.0))
+    method_upd, echo_upd = 0, 0
     for g in groups:
         m = len(g["x0"])
-        per = amp_updates(g["n"], g["gates"]) * (2 if g.get("metric", "fidelity") == "fidelity" else 1)
-        tupd += m * per
+        per = amp_updates(g["n"], g["gates"])
+        method_upd += m * per
+        if g.get("metric", "fidelity") == "fidelity":
+            echo_upd += m * per      # the noiseless inverse circuit that measures the fidelity
+    _release(torch)
+    t0 = time.perf_counter()
+    qs.run_trajectories(groups, 1e-3, 1e-2, 7, dtype="c128", with_stats=False, fuse=False)
+    t_plain = time.perf_counter() - t0
+    _release(torch)
     out["trajectories"] = {"workload": "4096 trajectories, 12/16/20 qubits 2:1:1, QFT + Grover(12,16), "
                                        "sigma=1e-2, p=1e-3, complex64",
                            "seconds": dt, "trajectories_per_s": len(met) / dt,
-                           "amp_updates_per_s": tupd / dt,
-                           "histogram_0_1_10bins": hist.tolist(), "mean_metric": float(met.mean())}
+                           "amp_updates_per_s": method_upd / dt,
+                           "amp_updates_note": "the circuits' own gates; the fidelity echo (the inverse noiseless "
+                                               "circuit of the QFT groups, %.3g updates) is overhead and not counted"
+                                               % echo_upd,
+                           "echo_share_of_updates": echo_upd / (method_upd + echo_upd),
+                           "histogram_0_1_10bins": hist.tolist(), "mean_metric": float(met.mean()),
+                           "plain_fp64_seconds": t_plain, "speedup_vs_plain_fp64": t_plain / dt,
+                           "plain_fp64_note": "qs_run_trajectories with no_fusion = 1 on complex128: one launch "
+                                              "per gate step, flips applied to the states, double instructions"}
 
-    # Grover search, n = 24, floor(pi/4 sqrt(2^24)) = 3216 iterations, as one
-    # plan; success probability against sin^2((2j+1) theta), sin theta = 2^-12
+    # Grover search, n = 24, floor(pi/4 sqrt(2^24)) = 3216 iterations;
+    # success probability against sin^2((2j+1) theta), sin theta = 2^-12;
+    # complex64 renormalised in double precision every 256 iterations
     gn = 24
     gk = W.basis_index(24, gn)
     git = W.grover_iterations(gn)
-    ggates = W.grover_circuit(gn, gk, git)
-    want = math.sin((2 * git + 1) * math.asin(2.0 ** (-gn / 2))) ** 2
-    gro = {"workload": "Grover n=24, %d iterations (%d gates: 2 H layers and 2 one-amplitude phase flips "
-                       "per iteration)" % (git, len(ggates))}
+    gro = {}
     for dt_name, B in (("c64", 8), ("c128", 16)):
+        search = paper.GroverSearch(gn, gk, git, dt_name)
         gs = qs.State(gn, dt_name)
-        gp = qs.Plan(gn, dt_name, ggates)
-        run = lambda: (gs.init_basis(0), gp.execute(gs))
+        run = lambda: search.run(gs)
         run()
         ms = _time(torch, run)
         p_succ = gs.prob(gk)
-        gro[dt_name] = {"ms": ms, "gates_per_s": len(ggates) / (ms / 1e3), "passes": gp.launches,
-                        "hbm_gbs": gp.launches * 2.0 * (B << gn) / (ms / 1e3) / 1e9,
+        want = search.closed_form()
+        gro[dt_name] = {"ms": ms, "gates_per_s": search.n_gates / (ms / 1e3), "passes": search.launches,
+                        "renormalised_every": 256 if search.renorm else None,
+                        "hbm_gbs": search.launches * 2.0 * (B << gn) / (ms / 1e3) / 1e9,
                         "success_probability": p_succ, "closed_form": want, "error": abs(p_succ - want)}
-        gro[dt_name]["frac_of_measured_hbm"] = gro[dt_name]["hbm_gbs"] / measured_peaks()[0]
+        gro[dt_name]["frac_of_measured_hbm"] = gro[dt_name]["hbm_gbs"] / hbm_peak
         gs.close()
-        del gp
+        del search
+        _release(torch)
+    gro["workload"] = "Grover n=24, %d iterations (2 H layers and 2 one-amplitude phase flips per iteration)" % git
     out["grover_n24"] = gro
     return out
 
@@ -399,13 +602,15 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--dtype", choices=["c64", "c128"], default="c64")
+    ap.add_argument("--dtype", choices=["c64", "c128"], default="c128")
+    ap.add_argument("--arith", choices=["default", "f64"], default="default",
+                    help="complex128 fused passes: double-single (default) or double-precision instructions")
     ap.add_argument("--no-fuse", action="store_true")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-secondary", action="store_true",
-                    help="skip the complex128, adjoint and trajectory measurements")
+                    help="skip the complex64, adjoint, trajectory and Grover measurements")
     ap.add_argument("--ref-budget", type=float, default=15.0)
     ap.add_argument("--paper-tables", action="store_true",
                     help="run the paper's tables (QFT circuit vs FFT, HT, Table hod, Figs. 20d/20o, "
@@ -440,12 +645,14 @@ def main():
             print(json.dumps({"paper_tables": paper_tables(torch, qs)}), flush=True)
         return
 
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    peaks = {"f32": qs.alu_peak("f32"), "f64": qs.alu_peak("f64")}
     n = args.n
     gates = W.random_circuit(n, LAYERS, seed=SEED + rank)
     upd = amp_updates(n, gates)
-    plan = qs.Plan(n, args.dtype, gates, fuse=not args.no_fuse)
+    arith = args.arith if args.dtype == "c128" else "default"
+    plan = qs.Plan(n, args.dtype, gates, fuse=not args.no_fuse, arith=arith)
     state = qs.State(n, args.dtype)
-    amp_bytes = 8 if args.dtype == "c64" else 16
 
     def step():
         state.init_basis(0)
@@ -455,10 +662,8 @@ def main():
         step()
     torch.cuda.synchronize()
 
-    # timed region: device events on the launching stream, plus per-launch
-    # events recorded by the library around every pass
-    plan.set_timing(True)
-    plan.timing()
+    # timed region: device events on the launching stream; no per-launch
+    # events inside it
     stream = torch.cuda.current_stream()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -469,7 +674,6 @@ def main():
     sampler.start()
     time.sleep(0.3)
     ev0.record(stream)
-    kern_ms, kern_n = 0.0, 0
     for _ in range(args.steps):
         step()
     ev1.record(stream)
@@ -477,60 +681,41 @@ def main():
     clocks = sampler.stop()
     if dist:
         dist.barrier()
-    ms, nl = plan.timing()
-    kern_ms += ms
-    kern_n += nl
-    plan.set_timing(False)
     ms_per_step, value = aggregate(ev0.elapsed_time(ev1) / args.steps, upd, world, dist)
 
-    # roofline of the dominant kernel (the fused pass, or the pair sweep),
-    # measured on its own launches with per-launch CUDA events
-    peak_gbs, peak_src = measured_peaks()
+    # roofline of the dominant kernel: a separate pass of steps with a CUDA
+    # event pair around every launch, on the launching stream
+    roof_steps = 2
+    plan.set_timing(True)
+    plan.timing()
+    for _ in range(roof_steps):
+        step()
+    kern_ms, kern_n = plan.timing()
+    plan.set_timing(False)
     sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
-    per_launch_ms = kern_ms / max(1, kern_n)
-    launches_per_step = kern_n / args.steps
-    if args.no_fuse:
-        # algorithmic bytes: one read and one write of every touched amplitude
-        bytes_step = sum(2 * amp_bytes * (1 << (n - len(g.controls))) for g in gates)
-    else:
-        bytes_step = launches_per_step * 2 * (amp_bytes << n)   # one read + one write per pass
-    flops_step = sum(16 * (1 << n) for g in gates if g.kind == "MATRIX")   # 8 multiply-adds per amplitude
-    kern_s_step = kern_ms / args.steps / 1e3
-    hbm_view = {"achieved": bytes_step / kern_s_step / 1e9, "peak": peak_gbs, "unit": "GB/s",
-                "frac": bytes_step / kern_s_step / 1e9 / peak_gbs, "peak_source": peak_src}
-    if args.dtype == "c64":
-        alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12     # FP32 lanes x 2 flops x SM clock
-        alu_src = "152 SMs x 128 FP32 lanes x 2 flops x %.0f MHz (measured SM clock)" % sm_mhz
-    else:
-        alu_peak = 1.25                                   # nominal FP64 rate of the part
-        alu_src = "nominal FP64 1.25 TFLOP/s"
-    alu_view = {"achieved": flops_step / kern_s_step / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": flops_step / kern_s_step / 1e12 / alu_peak, "peak_source": alu_src}
-    t_hbm = bytes_step / (peak_gbs * 1e9)
-    t_alu = flops_step / (alu_peak * 1e12)
-    main = alu_view if t_alu > t_hbm else hbm_view
-    # DRAM traffic of one fused-pass launch from one ncu capture of this
-    # kernel at n = 26 (1013.5 MB read + write per launch), scaled to n by the
-    # amplitudes processed; only valid for the complex64 fused kernel
-    traffic = 1013.5e6 * (1 << (n - 26)) if (args.dtype == "c64" and not args.no_fuse) else None
-    roof = {"bound": "alu" if t_alu > t_hbm else "hbm", "achieved": main["achieved"], "peak": main["peak"],
-            "unit": main["unit"], "frac": main["frac"], "traffic": traffic, "traffic_unit": "bytes per launch",
-            "kernel": ("k_fused_c64" if args.dtype == "c64" else "k_fused<double,4>") if not args.no_fuse else "k_pair",
-            "peak_source": main["peak_source"], "launches_timed": kern_n,
-            "kernel_ms_per_launch": per_launch_ms, "kernel_ms_per_step": kern_ms / args.steps,
-            "hbm_view": hbm_view, "alu_view": alu_view}
-    bytes_per_launch = 2 * (amp_bytes << n)
+    roof = rooflines(args, n, gates, kern_ms / roof_steps, kern_n / roof_steps, sm_mhz, sms, peaks)
+    roof.update({"launches_timed": kern_n, "steps_timed": roof_steps,
+                 "kernel_ms_per_launch": kern_ms / max(1, kern_n), "kernel_ms_per_step": kern_ms / roof_steps,
+                 "timing": "per-launch CUDA events in a separate pass of %d steps after the timed region"
+                           % roof_steps})
 
+    dtype_name = {"c64": "f32", "c128": "f64"}[args.dtype]
     line = {
         "metric": "amp-updates/s", "value": value, "unit": "amp-updates/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32" if args.dtype == "c64" else "f64",
+        "vs_baseline": None, "dtype": dtype_name,
+        "arith": ("double-single: each double split into two floats (48 significant bits), gates by "
+                  "error-free products and sums on the FP32 pipe; state, copies and reductions in FP64; "
+                  "parity vs the FP64 oracle <= 1e-12"
+                  if (args.dtype == "c128" and arith != "f64" and not args.no_fuse) else
+                  ("FP64 instructions" if args.dtype == "c128" else "FP32 instructions, FP64 reductions")),
         "data": "synthetic", "config": workload_config(args, world),
         "gates_per_s": world * len(gates) / (ms_per_step / 1e3),
-        "hbm_gbs_algorithmic": world * bytes_step / (ms_per_step / 1e3) / 1e9,
+        "hbm_gbs_algorithmic": world * roof["views"]["hbm"]["achieved"] * roof["kernel_ms_per_step"] / ms_per_step,
         "passes_per_step": plan.launches,
         "roofline": roof,
+        "peaks_measured": {"fp32_fma_per_s": peaks["f32"], "fp64_fma_per_s": peaks["f64"], "sms": sms},
         "gpu_launches": args.steps * (plan.launches + 1),
         "clocks": clocks,
     }
@@ -539,12 +724,12 @@ def main():
     # in from host memory (qs_apply_circuit copies, plans and launches), the
     # final state comes back to pinned host memory (qs_copy_out)
     if not args.no_e2e:
+        import ctypes
         host = torch.empty(1 << n, dtype=torch.complex64 if args.dtype == "c64" else torch.complex128,
                            pin_memory=True)
         hbuf = host.numpy()
-        import ctypes
         garr = qs.gates_to_abi(gates)
-        opts = qs._opts(not args.no_fuse)
+        opts = qs._opts(not args.no_fuse, 0, arith)
 
         def e2e_step():
             qs.check(qs.lib().qs_init_basis(state.handle, 0))
@@ -554,7 +739,7 @@ def main():
         e2e_step()
         if dist:
             dist.barrier()
-        k = max(1, min(args.steps, 5))
+        k = max(1, min(args.steps, 3))
         esampler = ClockSampler(local)
         esampler.start()
         step_ms = []
@@ -577,19 +762,17 @@ def main():
                        "d2h_copy_ms": tc * 1e3, "d2h_gbs": hbuf.nbytes / tc / 1e9,
                        "host_buffer_pinned": bool(host.is_pinned())}
         del host
+        _release(torch)
         # pipelined: the same steps on two states and two streams, each step's
         # copy-out overlapping the next step's passes; the serial figures stay
         # beside it
         try:
             pipe = e2e_pipelined(torch, qs, state, n, args.dtype, garr, len(gates), opts,
-                                 max(4, min(args.steps, 6)), dist, local)
+                                 max(3, min(args.steps, 4)), dist, local)
         except (RuntimeError, MemoryError) as exc:
             pipe = None
             line["e2e"]["pipelined_unavailable"] = str(exc).splitlines()[0][:200] if str(exc) else type(exc).__name__
-        # hand the pinned host buffers back to the system (torch caches them)
-        release = getattr(torch._C, "_host_emptyCache", None)
-        if release is not None:
-            release()
+        _release(torch)
         if pipe is not None:
             serial = line["e2e"]
             line["e2e"] = {"value": world * upd / (pipe["ms_per_step"] / 1e3), "unit": "amp-updates/s",
@@ -598,12 +781,15 @@ def main():
                            "serial": {k2: serial[k2] for k2 in ("value", "ms_per_step", "steps", "step_ms", "clocks",
                                                                 "d2h_copy_ms", "d2h_gbs", "host_buffer_pinned")}}
 
-    if not args.no_secondary and rank == 0:
-        line["secondary"] = secondary(args, torch, qs, state if args.dtype == "c64" else None)
+    if not args.no_secondary and rank == 0 and n == N_QUBITS:
+        step()   # the headline state for the complex64 distance
+        line["secondary"] = secondary(args, torch, qs, state if args.dtype == "c128" else None, peaks, sms,
+                                      sm_mhz)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        state.close()
         del state
-        torch.cuda.empty_cache()
+        _release(torch)
         cb = cpu_baseline(args.dtype)
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
     if rank == 0:

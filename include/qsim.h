@@ -507,6 +507,18 @@ qs_status qs_copy_out_async(qs_state *s, void *host, size_t bytes);
  * message of an asynchronous failure. */
 qs_status qs_sync(qs_state *s);
 
+/* --------------------------------------------------------------------- */
+/* Measurement service (no counterpart in the paper)                       */
+/* --------------------------------------------------------------------- */
+
+/* Measured rate of fused multiply-add instructions on the current device,
+ * in lane operations per second (kind 0: single precision, kind 1: double
+ * precision): a kernel of eight independent FMA chains per thread on eight
+ * 256-thread CTAs per SM, timed with CUDA events after a warm-up launch.
+ * These are the denominators of the arithmetic rooflines.  Synchronous;
+ * allocates and frees a small sink buffer.  Changes no device setting. */
+qs_status qs_alu_peak(int kind, double *fma_per_s);
+
 /* Thread-local message describing the last failure of this thread. */
 const char *qs_last_error(void);
 

@@ -53,19 +53,30 @@ class OrNoise(ctypes.Structure):
     ]
 
 
+# -O3 without contraction: every C operation rounds once, the same on x86 and
+# Arm hosts (no -march=native: the library and the oracle are built on
+# machines of both kinds and must give the same numbers there).
+CFLAGS = ["-O3", "-ffp-contract=off", "-std=c11", "-fPIC", "-shared", "-D_DEFAULT_SOURCE"]
+
+
 def build(force: bool = False) -> str:
     """Compiles qs_oracle.c into _build/libqs_oracle.so (OpenMP when available)."""
+    stamp = _LIB_PATH + ".flags"
+    flags = " ".join(CFLAGS)
     if not force and os.path.exists(_LIB_PATH) and \
-            os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
+            os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC) and \
+            os.path.exists(stamp) and open(stamp).read() == flags:
         return _LIB_PATH
     os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
     tmp = _LIB_PATH + ".tmp%d" % os.getpid()
-    base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-D_DEFAULT_SOURCE", "-o", tmp, _SRC, "-lm"]
+    base = ["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm"]
     try:
         subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
     except subprocess.CalledProcessError:
         subprocess.run(base, check=True, capture_output=True)
     os.replace(tmp, _LIB_PATH)
+    with open(stamp, "w") as f:
+        f.write(flags)
     return _LIB_PATH
 
 

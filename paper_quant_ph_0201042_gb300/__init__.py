@@ -137,6 +137,7 @@ _SIGS = {
                           ctypes.POINTER(QsGate), ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)],
     "qs_shard_pack": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p],
     "qs_shard_unpack": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p],
+    "qs_alu_peak": [ctypes.c_int, ctypes.POINTER(ctypes.c_double)],
     "qs_copy_out": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t],
     "qs_copy_out_async": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t],
     "qs_sync": [ctypes.c_void_p],
@@ -436,6 +437,14 @@ def run_trajectories(groups: Sequence, p: float, sigma: float, seed: int, dtype:
                                     met.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                     st.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)) if st is not None else None))
     return met[:total], (st[:total] if st is not None else None)
+
+
+def alu_peak(kind: str = "f32") -> float:
+    """Measured FMA lane operations per second on the current device
+    (qs_alu_peak): kind 'f32' or 'f64'."""
+    r = ctypes.c_double()
+    check(lib().qs_alu_peak({"f32": 0, "f64": 1}[kind], ctypes.byref(r)))
+    return r.value
 
 
 def batch_groups(batch) -> list:
