@@ -404,6 +404,29 @@ def secondary(args, torch, qs, state128, peaks, sms, sm_mhz):
         d = (s64.tensor.to(torch.complex128) - state128.tensor).abs().pow(2).sum().sqrt().item()
         c64["state_error_vs_c128"] = d
     out["c64"] = c64
+
+    # double-precision reductions (norm, Pauli expectation, inner product) at
+    # n = 30: bytes read per call against HBM; per-thread float-pair
+    # accumulation, double precision across threads
+    red = {}
+    zstr, xstr = "Z" * n, "X" + "Z" * (n - 1)
+    for dt_name, st, B in (("c64", s64, 8), ("c128", state128, 16)):
+        if st is None:
+            continue
+        other = qs.State(n, dt_name).init_basis(0)
+        r = {}
+        for name, fn, nbytes in (("norm", lambda: st.norm(), B << n),
+                                 ("expect_Z", lambda: st.expect(zstr), B << n),
+                                 ("expect_XZ", lambda: st.expect(xstr), 2 * (B << n)),
+                                 ("inner", lambda: st.inner(other), 2 * (B << n))):
+            fn()
+            ms = _time(torch, fn, reps=5)
+            r[name] = {"ms": ms, "hbm_gbs": nbytes / (ms / 1e3) / 1e9,
+                       "frac_of_measured_hbm": nbytes / (ms / 1e3) / 1e9 / hbm_peak}
+        r["fp64_pipe_ms_if_two_dfma_per_amplitude"] = (2 << n) / peaks["f64"] * 1e3
+        red[dt_name] = r
+        other.close()
+    out["reductions_n30"] = red
     s64.close()
     del p64
     _release(torch)

@@ -392,7 +392,8 @@ struct alignas(16) POp {
     uint8_t type, cls, tsel, tpos;
     uint8_t rmask, rval;
     uint8_t fast;          // state-vector fast paths: 1 uncontrolled general gate on a register slot,
-                           // 2 X deferred into the index mask, 3 uncontrolled general gate on a lane bit
+                           // 2 X deferred into the index mask, 3 uncontrolled general gate on a lane bit,
+                           // 4 / 5 as 1 / 3 for a real matrix (RY, U_R, ...)
     uint8_t pad0;
     uint32_t pad1;
     uint16_t tmask, tval;
@@ -444,6 +445,24 @@ __device__ __forceinline__ void pair_inplace(float2 &x, float2 &y, const Mat4<fl
     x.y = fmaf(m.u00.x, x.y, A);
     y.x = fmaf(m.u11.x, y.x, D);
     y.y = fmaf(m.u11.x, y.y, C);
+}
+
+// (x, y) <- (a x + b y, c x + d y) for a real matrix [[a, b], [c, d]]:
+// four multiply-adds per amplitude instead of eight
+template <int T, int NA>
+__device__ __forceinline__ void s_real(float2 (&v)[NA], float a, float b, float c, float d, uint32_t xm) {
+    if ((xm >> T) & 1) {   // deferred exchange on this slot: X U X
+        float t = a; a = d; d = t;
+        t = b; b = c; c = t;
+    }
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+        if ((j >> T) & 1) continue;
+        const int j1 = j | (1 << T);
+        const float2 x = v[j], y = v[j1];
+        v[j] = make_float2(fmaf(a, x.x, b * y.x), fmaf(a, x.y, b * y.y));
+        v[j1] = make_float2(fmaf(c, x.x, d * y.x), fmaf(c, x.y, d * y.y));
+    }
 }
 
 template <int T, bool PRED, int NA>
@@ -623,6 +642,7 @@ __global__ void __launch_bounds__(32 << QS_WB64, QS_FUSED_MINBLOCKS) k_fused_c64
             // values change with the trajectory's Pauli frame)
             int fast = int((hd.y >> 16) & 0xff);
             if (TRAJ && fast == 2) fast = 0;
+            if (TRAJ && fast >= 4) fast = fast == 4 ? 1 : 3;   // a trajectory's matrix need not be real
             if (fast) {
                 // the common cases without the general dispatch: no predicate
                 // work and no class tests
@@ -639,7 +659,23 @@ __global__ void __launch_bounds__(32 << QS_WB64, QS_FUSED_MINBLOCKS) k_fused_c64
                 const float4 f0 = cs4[0], f1 = cs4[1];
                 const Mat4<float> mf = {make_float2(f0.x, f0.y), make_float2(f0.z, f0.w), make_float2(f1.x, f1.y),
                                         make_float2(f1.z, f1.w)};
-                if (fast == 1) {
+                if (fast == 4) {
+                    const float a = f0.x, b = f0.z, c = f1.x, d = f1.z;
+                    if (tp == 0) s_real<0, NA>(v, a, b, c, d, xm);
+                    else if (tp == 1) s_real<1, NA>(v, a, b, c, d, xm);
+                    else if (tp == 2) s_real<2, NA>(v, a, b, c, d, xm);
+                    else if (tp == 3) s_real<3, NA>(v, a, b, c, d, xm);
+                    else s_real<(RB64 > 4 ? 4 : 0), NA>(v, a, b, c, d, xm);
+                } else if (fast == 5) {
+                    const int m = 1 << tp;
+                    const bool hi = (lane >> tp) & 1;
+                    const float cs = hi ? f1.z : f0.x, co = hi ? f1.x : f0.z;
+#pragma unroll
+                    for (int j = 0; j < NA; ++j) {
+                        const float2 o = shfl<float>(v[j], m);
+                        v[j] = make_float2(fmaf(cs, v[j].x, co * o.x), fmaf(cs, v[j].y, co * o.y));
+                    }
+                } else if (fast == 1) {
                     if (tp == 0) s_gen<0, false, NA>(v, mf, xm, 0, 0);
                     else if (tp == 1) s_gen<1, false, NA>(v, mf, xm, 0, 0);
                     else if (tp == 2) s_gen<2, false, NA>(v, mf, xm, 0, 0);
@@ -1320,6 +1356,8 @@ void convert_c64(const PassDesc<float> &D, const std::vector<FOp<float>> &ops, P
         else if (f.type == OP_LANE && f.cls != GC_X && f.cls != GC_HB && f.rmask == 0 && f.tmask == 0 &&
                  f.omask == 0)
             q.fast = 3;
+        if ((q.fast == 1 || q.fast == 3) && f.u[1] == 0 && f.u[3] == 0 && f.u[5] == 0 && f.u[7] == 0)
+            q.fast = uint8_t(q.fast + 3);   // real matrix
         if (f.type == OP_XPOSE) {
             // position of each high tile bit in the old tile order
             // (register index bits above the warp bits, warp bits above the lanes)

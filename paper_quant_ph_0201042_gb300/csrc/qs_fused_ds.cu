@@ -92,6 +92,22 @@ __device__ __forceinline__ camp rmad2(const ccst &a, const camp &x, const ccst &
     return o;
 }
 
+// A 2x2 op (general, real or Hadamard butterfly) on the pair (x, y).
+__device__ __forceinline__ void pair_op(int type, const ccst &u00, const ccst &u01, const ccst &u10, const ccst &u11,
+                                        camp &x, camp &y) {
+    if (type == D_HB) {
+        ds::butterfly(x, y);
+    } else if (type == D_REAL) {
+        const camp nx = rmad2(u00, x, u01, y), ny = rmad2(u10, x, u11, y);
+        x = nx;
+        y = ny;
+    } else {
+        const camp nx = ds::cmad2(u00, x, u01, y), ny = ds::cmad2(u10, x, u11, y);
+        x = nx;
+        y = ny;
+    }
+}
+
 // logical index of pair p with a zero inserted at bit t
 __device__ __forceinline__ uint32_t pair_index(uint32_t p, int t) {
     return ((p >> t) << (t + 1)) | (p & ((1u << t) - 1u));
@@ -169,17 +185,7 @@ __global__ void __launch_bounds__(DTHREADS, DMINBLOCKS) k_fused_ds(double2 *__re
                         amp[q1] = st(x);
                         continue;
                     }
-                    if (type == D_HB) {
-                        ds::butterfly(x, y);
-                    } else if (type == D_REAL) {
-                        const camp nx = rmad2(u00, x, u01, y), ny = rmad2(u10, x, u11, y);
-                        x = nx;
-                        y = ny;
-                    } else {
-                        const camp nx = ds::cmad2(u00, x, u01, y), ny = ds::cmad2(u10, x, u11, y);
-                        x = nx;
-                        y = ny;
-                    }
+                    pair_op(type, u00, u01, u10, u11, x, y);
                     amp[q0] = st(x);
                     amp[q1] = st(y);
                 }

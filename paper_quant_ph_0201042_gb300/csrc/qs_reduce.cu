@@ -4,9 +4,20 @@
 // Pauli expectation values and inner products (the fidelity of Sec. 5.2).
 //
 // Two deterministic levels: RED_BLOCKS blocks each sum a fixed grid-stride
-// slice of the vector (double accumulators, fixed shuffle tree), then one block
-// sums the RED_BLOCKS partials in a fixed order.  The result stays on the
-// device (s->result) and is copied to pinned host memory by the caller.
+// slice of the vector, then one block sums the RED_BLOCKS partials in a fixed
+// order.  The result stays on the device (s->result) and is copied to pinned
+// host memory by the caller.
+//
+// Each thread accumulates its slice in double-single arithmetic (qs_ds.cuh):
+// a product of two amplitude components is an exact pair of floats (plus the
+// cross terms of their low parts for a complex128 state, whose doubles are
+// split into float pairs with integer instructions), added into a float-pair
+// accumulator with TwoSum.  The per-thread sums (48 significant bits) become
+// doubles once, and the warp, block and final sums run in double precision.
+// On this part the double-precision pipe issues about a sixty-fourth of the
+// single-precision rate, so two double multiply-adds per amplitude would take
+// longer than reading the amplitude from HBM.
+#include "qs_ds.cuh"
 #include "qs_internal.cuh"
 
 namespace qs {
@@ -43,6 +54,37 @@ __device__ __forceinline__ double2 ld(const cplx<R> *a, uint64_t i) {
     return make_double2(double(v.x), double(v.y));
 }
 
+// An amplitude as double-single components (re = rh + rl, im = ih + il).
+__device__ __forceinline__ ds::camp lds(const float2 *a, uint64_t i) {
+    const float2 v = a[i];
+    return {v.x, 0.f, v.y, 0.f};
+}
+__device__ __forceinline__ ds::camp lds(const double2 *a, uint64_t i) {
+    const double2 v = a[i];
+    return ds::load(v.x, v.y);
+}
+
+// A float-pair accumulator: s = h + l.  LOWS: the components have low parts
+// (complex128); complex64 components are single floats.
+template <bool LOWS>
+struct DAcc {
+    float h = 0.f, l = 0.f;
+    // s += sg * (a * b) for float pairs a, b (sg = +1 or -1); the product of
+    // the two low parts is dropped (2^-48 of the term)
+    __device__ __forceinline__ void add(float ah, float al, float bh, float bl, float sg) {
+        const float p = ds::mul(sg * ah, bh);
+        float e = ds::fma(sg * ah, bh, -p);
+        if (LOWS) {
+            e = ds::fma(sg * ah, bl, e);
+            e = ds::fma(sg * al, bh, e);
+        }
+        float t, r;
+        ds::two_sum(h, p, t, r);
+        ds::fast_two_sum(t, ds::add(l, ds::add(r, e)), h, l);
+    }
+    __device__ __forceinline__ double value() const { return double(h) + double(l); }
+};
+
 // kind RED_NORM: sum |a_i|^2
 // kind RED_PROB_BIT: sum over i with (i & arg0) != 0 of |a_i|^2
 // kind RED_PAULI: sum_i conj(a[i ^ arg0]) a[i] (-1)^popcount(i & arg1)
@@ -52,31 +94,31 @@ __global__ void __launch_bounds__(RED_THREADS) k_partial(const cplx<R> *__restri
                                                          const cplx<R> *__restrict__ b, uint64_t N,
                                                          uint64_t arg0, uint64_t arg1,
                                                          double2 *__restrict__ partial) {
-    double2 acc = make_double2(0.0, 0.0);
+    DAcc<sizeof(R) == 8> ar, ai;
     const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
     for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += stride) {
-        const double2 v = ld<R>(a, i);
-        if (KIND == RED_NORM) {
-            acc.x = fma(v.x, v.x, acc.x);
-            acc.x = fma(v.y, v.y, acc.x);
-        } else if (KIND == RED_PROB_BIT) {
-            if (i & arg0) {
-                acc.x = fma(v.x, v.x, acc.x);
-                acc.x = fma(v.y, v.y, acc.x);
-            }
+        if (KIND == RED_PROB_BIT && !(i & arg0)) continue;
+        const ds::camp v = lds(a, i);
+        if (KIND == RED_NORM || KIND == RED_PROB_BIT) {
+            ar.add(v.rh, v.rl, v.rh, v.rl, 1.f);
+            ar.add(v.ih, v.il, v.ih, v.il, 1.f);
         } else if (KIND == RED_PAULI) {
-            const double2 w = ld<R>(a, i ^ arg0);
-            const double sg = (__popcll(i & arg1) & 1) ? -1.0 : 1.0;
+            const ds::camp w = lds(a, i ^ arg0);
+            const float sg = (__popcll(i & arg1) & 1) ? -1.f : 1.f;
             // conj(w) * v
-            acc.x = fma(sg, w.x * v.x + w.y * v.y, acc.x);
-            acc.y = fma(sg, w.x * v.y - w.y * v.x, acc.y);
+            ar.add(w.rh, w.rl, v.rh, v.rl, sg);
+            ar.add(w.ih, w.il, v.ih, v.il, sg);
+            ai.add(w.rh, w.rl, v.ih, v.il, sg);
+            ai.add(w.ih, w.il, v.rh, v.rl, -sg);
         } else {  // RED_INNER: conj(v) * w
-            const double2 w = ld<R>(b, i);
-            acc.x += v.x * w.x + v.y * w.y;
-            acc.y += v.x * w.y - v.y * w.x;
+            const ds::camp w = lds(b, i);
+            ar.add(v.rh, v.rl, w.rh, w.rl, 1.f);
+            ar.add(v.ih, v.il, w.ih, w.il, 1.f);
+            ai.add(v.rh, v.rl, w.ih, w.il, 1.f);
+            ai.add(v.ih, v.il, w.rh, w.rl, -1.f);
         }
     }
-    acc = block_sum(acc);
+    double2 acc = block_sum(make_double2(ar.value(), ai.value()));
     if (threadIdx.x == 0) partial[blockIdx.x] = acc;
 }
 
