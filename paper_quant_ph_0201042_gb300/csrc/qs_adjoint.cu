@@ -278,6 +278,7 @@ struct AdjFPass {
     uint8_t tile_pos[16];
     uint8_t run_len[ADJ_MAX_OPS];
     uint8_t run_bit[ADJ_MAX_OPS];
+    uint8_t run_bit2[ADJ_MAX_OPS];   // second target bit of a two-bit run, 0xff for one bit
     uint8_t run_pre[ADJ_MAX_OPS];    // leading exchange steps of the run, applied at its load
 };
 
@@ -561,22 +562,35 @@ __global__ void __launch_bounds__(AF_THREADS, 2) k_adj_pass(cplx<R> *__restrict_
         __syncthreads();
         int k0 = 0;
         for (int r = 0; r < P.nrun; ++r) {
+            // A run acts on one or two tile bits, A = 2^t and B: each thread
+            // keeps NQ quadruples (i, i|A, i|B, i|A|B) of psi and lambda in
+            // registers (a one-bit run takes any other tile bit as B).  The
+            // pair arrays hold the quadruples as the pairs of the bit the
+            // current step needs: on A, (i, i|A) and (i|B, i|A|B); on B,
+            // (i, i|B) and (i|A, i|A|B); switching bits exchanges the middle
+            // elements (register moves).  Diagonal steps take either.
+            constexpr int NQ = NP / 2;
             const int t = P.run_bit[r], len = P.run_len[r];
-            const uint32_t tb = 1u << t;
-            // this thread's pairs (i0, i0 | tb) of the run's bit
+            const int t2 = P.run_bit2[r] != 0xff ? P.run_bit2[r] : (t == 0 ? 1 : 0);
+            const uint32_t A = 1u << t, B = 1u << t2;
+            const int lo = t < t2 ? t : t2, hi = t < t2 ? t2 : t;
             uint32_t i0[NP];
             bool ok[NP];
             cplx<R> px[NP], py[NP], lx[NP], ly[NP];
-            // the run's leading exchange steps (C-NOT-like, on the run's bit)
-            // become the choice of which element of the pair loads as x
+#pragma unroll
+            for (int j = 0; j < NQ; ++j) {
+                const uint32_t p = tid + uint32_t(j) * AF_THREADS;
+                const uint32_t x = ((p >> lo) << (lo + 1)) | (p & ((1u << lo) - 1u));
+                const uint32_t q = ((x >> hi) << (hi + 1)) | (x & ((1u << hi) - 1u));
+                ok[j] = ok[NQ + j] = p < T / 4;
+                i0[j] = q;
+                i0[NQ + j] = q | B;
+            }
+            // the run's leading exchange steps (C-NOT-like, on bit A) become
+            // the choice of which element of each pair on A loads as x
             bool flip[NP];
 #pragma unroll
-            for (int j = 0; j < NP; ++j) {
-                const uint32_t p = tid + uint32_t(j) * AF_THREADS;
-                ok[j] = p < T / 2;
-                i0[j] = ((p >> t) << (t + 1)) | (p & (tb - 1));
-                flip[j] = false;
-            }
+            for (int j = 0; j < NP; ++j) flip[j] = false;
             const int pre = P.run_pre[r];
             for (int k = k0; k < k0 + pre; ++k) {
                 const AdjFOp<R> &os = sops[k];
@@ -588,18 +602,33 @@ __global__ void __launch_bounds__(AF_THREADS, 2) k_adj_pass(cplx<R> *__restrict_
 #pragma unroll
             for (int j = 0; j < NP; ++j) {
                 if (ok[j]) {
-                    const uint32_t ia = flip[j] ? i0[j] | tb : i0[j], ib = ia ^ tb;
+                    const uint32_t ia = flip[j] ? i0[j] | A : i0[j], ib = ia ^ A;
                     px[j] = sp[ia]; py[j] = sp[ib];
                     lx[j] = sl[ia]; ly[j] = sl[ib];
                 }
             }
+            bool onB = false;   // the arrays hold the pairs of bit B
             for (int k = k0 + pre; k < k0 + len; ++k) {
                 const AdjFOp<R> &os = sops[k];
                 if ((base & os.om) != os.ov) continue;            // the same for the whole tile
+                const bool diagonal = os.mode == 2 || os.mode == 3;
+                const bool wantB = !diagonal && os.tpos == t2;
+                if (!diagonal && wantB != onB) {
+#pragma unroll
+                    for (int j = 0; j < NQ; ++j) {
+                        const cplx<R> a = py[j];
+                        py[j] = px[NQ + j]; px[NQ + j] = a;
+                        const cplx<R> c = ly[j];
+                        ly[j] = lx[NQ + j]; lx[NQ + j] = c;
+                        i0[NQ + j] = i0[j] | (wantB ? A : B);
+                    }
+                    onB = wantB;
+                }
+                const uint32_t tbv = onB ? B : A;
                 const int nang = os.nang;
                 R a0 = R(0), a1 = R(0);
-                if (os.cm == 0) step_on_pairs<R, NP, false>(os, base, tb, ok, i0, px, py, lx, ly, a0, a1);
-                else step_on_pairs<R, NP, true>(os, base, tb, ok, i0, px, py, lx, ly, a0, a1);
+                if (os.cm == 0) step_on_pairs<R, NP, false>(os, base, tbv, ok, i0, px, py, lx, ly, a0, a1);
+                else step_on_pairs<R, NP, true>(os, base, tbv, ok, i0, px, py, lx, ly, a0, a1);
                 if (nang > 0) {
                     const R s0 = warp_sum<R>(a0);
                     if (lane == 0) acc_add<R>(sacc[os.acc * AF_WARPS + warp], s0);
@@ -609,11 +638,22 @@ __global__ void __launch_bounds__(AF_THREADS, 2) k_adj_pass(cplx<R> *__restrict_
                     }
                 }
             }
+            // back to the pairs of bit A, then to shared memory
+            if (onB) {
+#pragma unroll
+                for (int j = 0; j < NQ; ++j) {
+                    const cplx<R> a = py[j];
+                    py[j] = px[NQ + j]; px[NQ + j] = a;
+                    const cplx<R> c = ly[j];
+                    ly[j] = lx[NQ + j]; lx[NQ + j] = c;
+                    i0[NQ + j] = i0[j] | B;
+                }
+            }
 #pragma unroll
             for (int j = 0; j < NP; ++j) {
                 if (ok[j]) {
-                    sp[i0[j]] = px[j]; sp[i0[j] | tb] = py[j];
-                    sl[i0[j]] = lx[j]; sl[i0[j] | tb] = ly[j];
+                    sp[i0[j]] = px[j]; sp[i0[j] | A] = py[j];
+                    sl[i0[j]] = lx[j]; sl[i0[j] | A] = ly[j];
                 }
             }
             k0 += len;
@@ -657,14 +697,20 @@ bool real_gens(const AdjStep &d) {
 
 // Orders a pass's steps (idx, in sweep order) into runs: the next step is the
 // first ready one (every earlier step it does not commute with already
-// placed) that is diagonal or targets the current run's bit; when none is,
-// the run ends and the first ready step opens the next.  Two steps commute
-// when every index bit they share is a control or the target of a diagonal
-// step for both (the test the pass planner uses), and moving a step past
-// steps it commutes with leaves every gradient term unchanged.  runs holds
-// (length, global target bit or -1 for a run of diagonal steps only).
+// placed) that is diagonal or targets one of the current run's bits (a run
+// takes up to two target bits; a second bit joins with the first step on it);
+// when none is, the run ends and the first ready step opens the next.  Two
+// steps commute when every index bit they share is a control or the target
+// of a diagonal step for both (the test the pass planner uses), and moving a
+// step past steps it commutes with leaves every gradient term unchanged.
+struct Run {
+    int len;    // steps
+    int bit;    // global target bit, -1 for a run of diagonal steps only
+    int bit2;   // second global target bit, -1 for none
+};
+
 void schedule_runs(const std::vector<int> &idx, const std::vector<AdjStep> &steps, const std::vector<HostOp> &hops,
-                   std::vector<int> &order, std::vector<std::pair<int, int>> &runs) {
+                   std::vector<int> &order, std::vector<Run> &runs) {
     const size_t m = idx.size();
     std::vector<uint64_t> sup(m), dg(m);
     std::vector<char> diag(m);
@@ -684,27 +730,35 @@ void schedule_runs(const std::vector<int> &idx, const std::vector<AdjStep> &step
         if (npred[k] == 0) ready.insert(int(k));
     order.clear();
     runs.clear();
-    int cur = -1, len = 0;
+    int cur = -1, cur2 = -1, len = 0;
     while (order.size() < m) {
         int pick = -1;
+        // a step on a bit the run already has, then one that opens a bit
         for (int k : ready) {
             const int b = hops[size_t(idx[size_t(k)])].bit;
-            if (diag[size_t(k)] || cur < 0 || b == cur) { pick = k; break; }
+            if (diag[size_t(k)] || b == cur || b == cur2) { pick = k; break; }
         }
+        if (pick < 0)
+            for (int k : ready)
+                if (cur < 0 || cur2 < 0) { pick = k; break; }
         if (pick < 0) {
-            runs.push_back({len, cur});
-            cur = -1;
+            runs.push_back({len, cur, cur2});
+            cur = cur2 = -1;
             len = 0;
             continue;
         }
-        if (!diag[size_t(pick)] && cur < 0) cur = hops[size_t(idx[size_t(pick)])].bit;
+        if (!diag[size_t(pick)]) {
+            const int b = hops[size_t(idx[size_t(pick)])].bit;
+            if (cur < 0) cur = b;
+            else if (b != cur && cur2 < 0) cur2 = b;
+        }
         order.push_back(idx[size_t(pick)]);
         ++len;
         ready.erase(pick);
         for (int sidx : succ[size_t(pick)])
             if (--npred[size_t(sidx)] == 0) ready.insert(sidx);
     }
-    if (len > 0) runs.push_back({len, cur});
+    if (len > 0) runs.push_back({len, cur, cur2});
 }
 
 // One tile pass of the fused reverse sweep, planned on the host: the tile's
@@ -714,7 +768,7 @@ void schedule_runs(const std::vector<int> &idx, const std::vector<AdjStep> &step
 struct SweepPass {
     std::vector<int> tile;
     std::vector<int> order;
-    std::vector<std::pair<int, int>> runs;
+    std::vector<Run> runs;
     std::vector<int> pre;
 };
 
@@ -744,9 +798,12 @@ bool plan_sweep(int n, int K, const std::vector<AdjStep> &steps, const std::vect
             if (steps[size_t(j)].cls != AC_DIAG &&
                 std::find(sp.tile.begin(), sp.tile.end(), hops[size_t(j)].bit) == sp.tile.end())
                 return false;
-        for (size_t r = 0, k = 0; r < sp.runs.size(); k += size_t(sp.runs[r].first), ++r) {
+        for (size_t r = 0, k = 0; r < sp.runs.size(); k += size_t(sp.runs[r].len), ++r) {
+            // leading exchanges on the run's first bit fold into the load
             int pre = 0;
-            while (pre < sp.runs[r].first && steps[size_t(sp.order[k + size_t(pre)])].cls == AC_X) ++pre;
+            while (pre < sp.runs[r].len && steps[size_t(sp.order[k + size_t(pre)])].cls == AC_X &&
+                   hops[size_t(sp.order[k + size_t(pre)])].bit == sp.runs[r].bit)
+                ++pre;
             sp.pre.push_back(pre);
         }
         out.push_back(std::move(sp));
@@ -778,8 +835,9 @@ cudaError_t fused_sweep(qs_state *s, const std::vector<AdjStep> &steps, const st
         if (sp.runs.size() > size_t(ADJ_MAX_OPS)) return cudaErrorInvalidValue;
         P.nrun = int(sp.runs.size());
         for (size_t r = 0; r < sp.runs.size(); ++r) {
-            P.run_len[r] = uint8_t(sp.runs[r].first);
-            P.run_bit[r] = uint8_t(sp.runs[r].second < 0 ? K - 1 : local[sp.runs[r].second]);
+            P.run_len[r] = uint8_t(sp.runs[r].len);
+            P.run_bit[r] = uint8_t(sp.runs[r].bit < 0 ? K - 1 : local[sp.runs[r].bit]);
+            P.run_bit2[r] = uint8_t(sp.runs[r].bit2 < 0 ? 0xff : local[sp.runs[r].bit2]);
             P.run_pre[r] = uint8_t(sp.pre[r]);
         }
         int nacc = 0;
@@ -1100,9 +1158,9 @@ extern "C" qs_status qs_adjoint_describe(int n, qs_dtype dt, const qs_gate *g, s
             out += "\n";
             size_t k = 0;
             for (size_t r = 0; r < plan[p].runs.size(); ++r) {
-                out += "run bit=" + std::to_string(plan[p].runs[r].second) + " pre=" + std::to_string(plan[p].pre[r]) +
-                       " steps=";
-                for (int i = 0; i < plan[p].runs[r].first; ++i, ++k)
+                out += "run bit=" + std::to_string(plan[p].runs[r].bit) + " bit2=" + std::to_string(plan[p].runs[r].bit2) +
+                       " pre=" + std::to_string(plan[p].pre[r]) + " steps=";
+                for (int i = 0; i < plan[p].runs[r].len; ++i, ++k)
                     out += (i ? "," : "") + std::to_string(plan[p].order[k]);
                 out += "\n";
             }

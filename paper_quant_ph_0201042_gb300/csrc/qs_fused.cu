@@ -659,7 +659,13 @@ __global__ void __launch_bounds__(32 << QS_WB64, QS_FUSED_MINBLOCKS) k_fused_c64
                 const float4 f0 = cs4[0], f1 = cs4[1];
                 const Mat4<float> mf = {make_float2(f0.x, f0.y), make_float2(f0.z, f0.w), make_float2(f1.x, f1.y),
                                         make_float2(f1.z, f1.w)};
-                if (fast == 4) {
+                if (fast == 1) {
+                    if (tp == 0) s_gen<0, false, NA>(v, mf, xm, 0, 0);
+                    else if (tp == 1) s_gen<1, false, NA>(v, mf, xm, 0, 0);
+                    else if (tp == 2) s_gen<2, false, NA>(v, mf, xm, 0, 0);
+                    else if (tp == 3) s_gen<3, false, NA>(v, mf, xm, 0, 0);
+                    else s_gen<(RB64 > 4 ? 4 : 0), false, NA>(v, mf, xm, 0, 0);
+                } else if (fast == 4) {
                     const float a = f0.x, b = f0.z, c = f1.x, d = f1.z;
                     if (tp == 0) s_real<0, NA>(v, a, b, c, d, xm);
                     else if (tp == 1) s_real<1, NA>(v, a, b, c, d, xm);
@@ -675,12 +681,6 @@ __global__ void __launch_bounds__(32 << QS_WB64, QS_FUSED_MINBLOCKS) k_fused_c64
                         const float2 o = shfl<float>(v[j], m);
                         v[j] = make_float2(fmaf(cs, v[j].x, co * o.x), fmaf(cs, v[j].y, co * o.y));
                     }
-                } else if (fast == 1) {
-                    if (tp == 0) s_gen<0, false, NA>(v, mf, xm, 0, 0);
-                    else if (tp == 1) s_gen<1, false, NA>(v, mf, xm, 0, 0);
-                    else if (tp == 2) s_gen<2, false, NA>(v, mf, xm, 0, 0);
-                    else if (tp == 3) s_gen<3, false, NA>(v, mf, xm, 0, 0);
-                    else s_gen<(RB64 > 4 ? 4 : 0), false, NA>(v, mf, xm, 0, 0);
                 } else {
                     const int m = 1 << tp;
                     const bool hi = (lane >> tp) & 1;
