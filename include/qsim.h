@@ -513,7 +513,7 @@ qs_status qs_sync(qs_state *s);
 
 /* Measured rate of fused multiply-add instructions on the current device,
  * in lane operations per second (kind 0: single precision, kind 1: double
- * precision): a kernel of eight independent FMA chains per thread on eight
+ * precision): a kernel of sixteen independent FMA chains per thread on eight
  * 256-thread CTAs per SM, timed with CUDA events after a warm-up launch.
  * These are the denominators of the arithmetic rooflines.  Synchronous;
  * allocates and frees a small sink buffer.  Changes no device setting. */

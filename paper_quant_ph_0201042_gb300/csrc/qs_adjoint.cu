@@ -295,6 +295,63 @@ __device__ __forceinline__ R pair_grad(const cplx<R> *g, cplx<R> px, cplx<R> py,
     return rdot<R>(lx, cmad2<R>(g[0], px, g[1], py)) + rdot<R>(ly, cmad2<R>(g[2], px, g[3], py));
 }
 
+// In-place forms of the updates: every output is written by the instruction
+// that reads its input for the last time, so the new value takes the old
+// one's register and the branches of the step dispatch join without moves.
+
+// x <- c x for complex c
+template <typename R>
+__device__ __forceinline__ void cmul_ip(cplx<R> c, cplx<R> &x) {
+    const R t1 = c.y * x.y, t2 = c.y * x.x;
+    x.x = fma(c.x, x.x, -t1);
+    x.y = fma(c.x, x.y, t2);
+}
+
+// (x, y) <- (a x + b y, c x + d y) with real a, b, c, d
+template <typename R>
+__device__ __forceinline__ void rmad_ip(R a, R b, R c, R d, cplx<R> &x, cplx<R> &y) {
+    const R bx = b * y.x, by = b * y.y, dx = d * y.x, dy = d * y.y;
+    y.x = fma(c, x.x, dx);
+    y.y = fma(c, x.y, dy);
+    x.x = fma(a, x.x, bx);
+    x.y = fma(a, x.y, by);
+}
+
+// (x, y) <- (u0 x + u1 y, u2 x + u3 y) with complex entries
+template <typename R>
+__device__ __forceinline__ void cmad_ip(cplx<R> u0, cplx<R> u1, cplx<R> u2, cplx<R> u3, cplx<R> &x, cplx<R> &y) {
+    R A = u1.x * y.y, B = -u1.y * y.y, C = u2.x * x.y, D = -u2.y * x.y;
+    A = fma(u1.y, y.x, A);    // new x.im: u1.re y.im + u1.im y.re
+    B = fma(u1.x, y.x, B);    // new x.re: u1.re y.re - u1.im y.im
+    C = fma(u2.y, x.x, C);    // new y.im: u2.re x.im + u2.im x.re
+    D = fma(u2.x, x.x, D);    // new y.re: u2.re x.re - u2.im x.im
+    B = fma(-u0.y, x.y, B);
+    A = fma(u0.y, x.x, A);
+    D = fma(-u3.y, y.y, D);
+    C = fma(u3.y, y.x, C);
+    x.x = fma(u0.x, x.x, B);
+    x.y = fma(u0.x, x.y, A);
+    y.x = fma(u3.x, y.x, D);
+    y.y = fma(u3.x, y.y, C);
+}
+
+// swap x and y where p holds, by masked XOR (no register moves)
+template <typename R> struct bits_t;
+template <> struct bits_t<float> { using type = uint32_t; };
+template <> struct bits_t<double> { using type = unsigned long long; };
+template <typename R>
+__device__ __forceinline__ void cswap_ip(bool p, cplx<R> &x, cplx<R> &y) {
+    using B = typename bits_t<R>::type;
+    const B m = p ? ~B(0) : B(0);
+    B xr, xi, yr, yi;
+    memcpy(&xr, &x.x, sizeof(B)); memcpy(&xi, &x.y, sizeof(B));
+    memcpy(&yr, &y.x, sizeof(B)); memcpy(&yi, &y.y, sizeof(B));
+    const B dr = (xr ^ yr) & m, di = (xi ^ yi) & m;
+    xr ^= dr; yr ^= dr; xi ^= di; yi ^= di;
+    memcpy(&x.x, &xr, sizeof(B)); memcpy(&x.y, &xi, sizeof(B));
+    memcpy(&y.x, &yr, sizeof(B)); memcpy(&y.y, &yi, sizeof(B));
+}
+
 // One step of a run on the thread's register pairs.  Pair steps act on the
 // run's bit (their controls exclude it); a diagonal step scales each element
 // by the entry its own target bit selects.  NA generators are accumulated.
@@ -304,10 +361,9 @@ __device__ __forceinline__ void run_exchange(uint32_t cm, uint32_t cv, const boo
                                              cplx<R> (&ly)[NP]) {
 #pragma unroll
     for (int j = 0; j < NP; ++j) {
-        if (!ok[j] || (CHK && (i0[j] & cm) != cv)) continue;
-        const cplx<R> x = px[j], l = lx[j];
-        px[j] = py[j]; py[j] = x;
-        lx[j] = ly[j]; ly[j] = l;
+        const bool p = ok[j] && (!CHK || (i0[j] & cm) == cv);
+        cswap_ip<R>(p, px[j], py[j]);
+        cswap_ip<R>(p, lx[j], ly[j]);
     }
 }
 
@@ -323,11 +379,10 @@ __device__ __forceinline__ void run_pair(const AdjFOp<R> &os, const bool (&ok)[N
 #pragma unroll
     for (int j = 0; j < NP; ++j) {
         if (!ok[j] || (CHK && (i0[j] & cm) != cv)) continue;
-        const cplx<R> x = px[j], y = py[j], lxv = lx[j], lyv = ly[j];
-        if (NA > 0) a0 += pair_grad<R>(g, x, y, lxv, lyv);
-        if (NA > 1) a1 += pair_grad<R>(h, x, y, lxv, lyv);
-        px[j] = cmad2<R>(u0, x, u1, y); py[j] = cmad2<R>(u2, x, u3, y);
-        lx[j] = cmad2<R>(u0, lxv, u1, lyv); ly[j] = cmad2<R>(u2, lxv, u3, lyv);
+        if (NA > 0) a0 += pair_grad<R>(g, px[j], py[j], lx[j], ly[j]);
+        if (NA > 1) a1 += pair_grad<R>(h, px[j], py[j], lx[j], ly[j]);
+        cmad_ip<R>(u0, u1, u2, u3, px[j], py[j]);
+        cmad_ip<R>(u0, u1, u2, u3, lx[j], ly[j]);
     }
 }
 
@@ -344,14 +399,14 @@ __device__ __forceinline__ void run_pair_real(const AdjFOp<R> &os, const bool (&
 #pragma unroll
     for (int j = 0; j < NP; ++j) {
         if (!ok[j] || (CHK && (i0[j] & cm) != cv)) continue;
-        const cplx<R> x = px[j], y = py[j], lxv = lx[j], lyv = ly[j];
         if (NA > 0) {
-            const R xx = rdot<R>(lxv, x), xy = rdot<R>(lxv, y), yx = rdot<R>(lyv, x), yy = rdot<R>(lyv, y);
+            const R xx = rdot<R>(lx[j], px[j]), xy = rdot<R>(lx[j], py[j]), yx = rdot<R>(ly[j], px[j]),
+                    yy = rdot<R>(ly[j], py[j]);
             a0 += g[0] * xx + g[1] * xy + g[2] * yx + g[3] * yy;
             if (NA > 1) a1 += h[0] * xx + h[1] * xy + h[2] * yx + h[3] * yy;
         }
-        px[j] = rmad2<R>(u0, x, u1, y); py[j] = rmad2<R>(u2, x, u3, y);
-        lx[j] = rmad2<R>(u0, lxv, u1, lyv); ly[j] = rmad2<R>(u2, lxv, u3, lyv);
+        rmad_ip<R>(u0, u1, u2, u3, px[j], py[j]);
+        rmad_ip<R>(u0, u1, u2, u3, lx[j], ly[j]);
     }
 }
 
@@ -367,13 +422,12 @@ __device__ __forceinline__ void run_pair_real_as(const AdjFOp<R> &os, const bool
 #pragma unroll
     for (int j = 0; j < NP; ++j) {
         if (!ok[j] || (CHK && (i0[j] & cm) != cv)) continue;
-        const cplx<R> x = px[j], y = py[j], lxv = lx[j], lyv = ly[j];
-        t = fma(lyv.x, x.x, t);
-        t = fma(lyv.y, x.y, t);
-        t = fma(-lxv.x, y.x, t);
-        t = fma(-lxv.y, y.y, t);
-        px[j] = rmad2<R>(u0, x, u1, y); py[j] = rmad2<R>(u2, x, u3, y);
-        lx[j] = rmad2<R>(u0, lxv, u1, lyv); ly[j] = rmad2<R>(u2, lxv, u3, lyv);
+        t = fma(ly[j].x, px[j].x, t);
+        t = fma(ly[j].y, px[j].y, t);
+        t = fma(-lx[j].x, py[j].x, t);
+        t = fma(-lx[j].y, py[j].y, t);
+        rmad_ip<R>(u0, u1, u2, u3, px[j], py[j]);
+        rmad_ip<R>(u0, u1, u2, u3, lx[j], ly[j]);
     }
     a0 += os.g0[2].x * t;
 }
@@ -382,16 +436,16 @@ template <typename R, int NA>
 __device__ __forceinline__ void diag_elem(cplx<R> d, cplx<R> g, cplx<R> h, cplx<R> &x, cplx<R> &l, R &a0, R &a1) {
     if (NA > 0) a0 += rdot<R>(l, cmul<R>(g, x));
     if (NA > 1) a1 += rdot<R>(l, cmul<R>(h, x));
-    x = cmul<R>(d, x);
-    l = cmul<R>(d, l);
+    cmul_ip<R>(d, x);
+    cmul_ip<R>(d, l);
 }
 
 // one imaginary diagonal generator entry i g: Re<l|i g x> = g (l.y x.x - l.x x.y)
 template <typename R>
 __device__ __forceinline__ void diag_elem_im(cplx<R> d, R g, cplx<R> &x, cplx<R> &l, R &a0) {
     a0 = fma(g, fma(l.y, x.x, -l.x * x.y), a0);
-    x = cmul<R>(d, x);
-    l = cmul<R>(d, l);
+    cmul_ip<R>(d, x);
+    cmul_ip<R>(d, l);
 }
 
 // DK: where the diagonal's bit lies.  0: the run's own bit (the pair's

@@ -1454,9 +1454,9 @@ qs_status plan_build(int n, qs_dtype dt, const std::vector<HostOp> &ops, const q
     P->RB = dt == QS_C64 ? RB64 : RB128;
     const int max_ops = o.max_ops_per_pass > 0 ? std::max(4, std::min(o.max_ops_per_pass, MAX_OPS)) : MAX_OPS;
     P->fused = !o.no_fusion && n >= LB + P->RB;
-    // complex128: double-single passes (n >= 12) unless the caller asks for
-    // double-precision instructions
-    const bool ds = dt == QS_C128 && o.c128_arith != QS_ARITH_F64 && n >= 12;
+    // complex128: double-single passes (registers of at least a tile) unless
+    // the caller asks for double-precision instructions
+    const bool ds = dt == QS_C128 && o.c128_arith != QS_ARITH_F64 && n >= ds_min_qubits();
     if (!P->fused) {
         P->ops = ops;
     } else if (ds) {

@@ -45,12 +45,25 @@ namespace qs {
 namespace {
 
 constexpr int LB = 5;                   // lane bits (contiguous rows of 32 amplitudes)
-constexpr int DK = 12;                  // tile bits
+#ifndef QS_DS_K
+#define QS_DS_K 12
+#endif
+#ifndef QS_DS_THREADS
+#define QS_DS_THREADS 256
+#endif
+#ifndef QS_DS_MINBLOCKS
+#define QS_DS_MINBLOCKS 3
+#endif
+#ifndef QS_DS_UNROLL
+#define QS_DS_UNROLL 1
+#endif
+constexpr int DK = QS_DS_K;             // tile bits
 constexpr int DH = DK - LB;             // high tile bits
 constexpr int DT = 1 << DK;             // amplitudes per tile
-constexpr int DTHREADS = 256;
+constexpr int DTHREADS = QS_DS_THREADS;
 constexpr int DMAX_OPS = 80;            // ops per pass
-constexpr int DMINBLOCKS = 3;
+constexpr int DMINBLOCKS = QS_DS_MINBLOCKS;
+constexpr int DUNROLL = QS_DS_UNROLL;     // pairs per loop iteration
 
 enum DsType : uint8_t { D_GEN = 0, D_REAL = 1, D_HB = 2, D_X = 3, D_DIAG = 4 };
 
@@ -175,6 +188,7 @@ __global__ void __launch_bounds__(DTHREADS, DMINBLOCKS) k_fused_ds(double2 *__re
             } else {
                 const int t = o.tbit;
                 const ccst u00 = cst(o.c), u01 = cst(o.c + 4), u10 = cst(o.c + 8), u11 = cst(o.c + 12);
+#pragma unroll DUNROLL
                 for (uint32_t p = tid; p < uint32_t(DT / 2); p += DTHREADS) {
                     const uint32_t i0 = pair_index(p, t), i1 = i0 | (1u << t);
                     if ((i0 & tm) != tv) continue;
@@ -232,7 +246,7 @@ struct DsPlan {
 };
 
 qs_status ds_plan_build(int n, const std::vector<HostOp> &ops, int max_ops, bool temp, DsPlan **out) {
-    if (n < DK) return fail(QS_EUNSUPPORTED, "double-single passes need n >= 12");
+    if (n < DK) return fail(QS_EUNSUPPORTED, "double-single passes need n >= the tile bits");
     DsPlan *P = new DsPlan();
     P->n = n;
     P->temp = temp;
@@ -365,6 +379,8 @@ cudaError_t ds_plan_run(DsPlan *P, double2 *state, cudaStream_t st, Plan *timing
 }
 
 int64_t ds_plan_launches(const DsPlan *P) { return int64_t(P->passes.size()); }
+
+int ds_min_qubits() { return DK; }
 
 std::string ds_plan_describe(const DsPlan *P) {
     std::string out;

@@ -183,6 +183,7 @@ struct DsPlan;
 qs_status ds_plan_build(int n, const std::vector<HostOp> &ops, int max_ops, bool temp, DsPlan **out);
 cudaError_t ds_plan_run(DsPlan *p, double2 *state, cudaStream_t st, Plan *timing);
 int64_t ds_plan_launches(const DsPlan *p);
+int ds_min_qubits();   // registers smaller than the tile use the double-instruction passes
 std::string ds_plan_describe(const DsPlan *p);
 void ds_plan_destroy(DsPlan *p);
 

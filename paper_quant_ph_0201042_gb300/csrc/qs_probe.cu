@@ -2,7 +2,7 @@
 // the arithmetic rooflines (no counterpart in the paper; a measurement
 // service of the library).
 //
-// Every thread runs eight independent FMA chains (enough to cover the
+// Every thread runs sixteen independent FMA chains (enough to cover the
 // pipes' latency) for a fixed number of iterations, on a grid of eight
 // 256-thread CTAs per SM.  The rate is FMA instructions times lanes per
 // second, from CUDA events around the second of two identical launches.  No
@@ -12,17 +12,23 @@
 namespace {
 
 constexpr int PROBE_THREADS = 256;
+constexpr int CHAINS = 16;   // independent FMA chains per thread
 
 template <typename R>
 __global__ void __launch_bounds__(PROBE_THREADS) k_fma_chains(R *__restrict__ sink, R a, R b, int iters) {
-    R x0 = R(threadIdx.x), x1 = x0 + R(1), x2 = x0 + R(2), x3 = x0 + R(3);
-    R x4 = x0 + R(4), x5 = x0 + R(5), x6 = x0 + R(6), x7 = x0 + R(7);
+    constexpr int C = CHAINS;
+    R x[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) x[c] = R(threadIdx.x) + R(c);
     for (int i = 0; i < iters; ++i) {
-        x0 = fma(x0, a, b); x1 = fma(x1, a, b); x2 = fma(x2, a, b); x3 = fma(x3, a, b);
-        x4 = fma(x4, a, b); x5 = fma(x5, a, b); x6 = fma(x6, a, b); x7 = fma(x7, a, b);
+#pragma unroll
+        for (int c = 0; c < C; ++c) x[c] = fma(x[c], a, b);
     }
     // one store per thread keeps the chains alive
-    sink[blockIdx.x * blockDim.x + threadIdx.x] = ((x0 + x1) + (x2 + x3)) + ((x4 + x5) + (x6 + x7));
+    R s = R(0);
+#pragma unroll
+    for (int c = 0; c < C; ++c) s += x[c];
+    sink[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
 template <typename R>
@@ -51,7 +57,7 @@ qs_status measure(int iters, double *per_s) {
     if (e1) cudaEventDestroy(e1);
     cudaFree(sink);
     if (e != cudaSuccess) return qs::cuda_fail(e, "qs_alu_peak: timing");
-    *per_s = double(blocks) * PROBE_THREADS * 8.0 * iters / (double(ms) * 1e-3);
+    *per_s = double(blocks) * PROBE_THREADS * double(CHAINS) * iters / (double(ms) * 1e-3);
     return QS_OK;
 }
 
@@ -59,7 +65,7 @@ qs_status measure(int iters, double *per_s) {
 
 extern "C" qs_status qs_alu_peak(int kind, double *fma_per_s) {
     if (!fma_per_s) return qs::fail(QS_EINVAL, "qs_alu_peak: NULL result");
-    if (kind == 0) return measure<float>(8192, fma_per_s);
-    if (kind == 1) return measure<double>(256, fma_per_s);
+    if (kind == 0) return measure<float>(4096, fma_per_s);
+    if (kind == 1) return measure<double>(128, fma_per_s);
     return qs::fail(QS_EINVAL, "qs_alu_peak: kind must be 0 (single) or 1 (double)");
 }
