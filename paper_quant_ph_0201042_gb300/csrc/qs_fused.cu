@@ -502,15 +502,26 @@ __device__ __forceinline__ void s_xdata(float2 (&v)[NA], uint32_t xm, int rm, in
 
 template <int T, int NA>
 __device__ __forceinline__ void s_hb(float2 (&v)[NA], uint32_t xm) {
-    const bool sw = (xm >> T) & 1;
+    // the deferred-exchange bit of the slot is the same across the warp: a
+    // branch, not a select per amplitude
+    if ((xm >> T) & 1) {
 #pragma unroll
-    for (int j = 0; j < NA; ++j) {
-        if ((j >> T) & 1) continue;
-        const int j1 = j | (1 << T);
-        const float2 x = v[j], y = v[j1];
-        const float2 sm = make_float2(x.x + y.x, x.y + y.y), df = make_float2(x.x - y.x, x.y - y.y);
-        v[j] = sw ? make_float2(-df.x, -df.y) : sm;
-        v[j1] = sw ? sm : df;
+        for (int j = 0; j < NA; ++j) {
+            if ((j >> T) & 1) continue;
+            const int j1 = j | (1 << T);
+            const float2 x = v[j], y = v[j1];
+            v[j] = make_float2(y.x - x.x, y.y - x.y);
+            v[j1] = make_float2(x.x + y.x, x.y + y.y);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < NA; ++j) {
+            if ((j >> T) & 1) continue;
+            const int j1 = j | (1 << T);
+            const float2 x = v[j], y = v[j1];
+            v[j] = make_float2(x.x + y.x, x.y + y.y);
+            v[j1] = make_float2(x.x - y.x, x.y - y.y);
+        }
     }
 }
 
@@ -748,10 +759,12 @@ __global__ void __launch_bounds__(32 << QS_WB64, QS_FUSED_MINBLOCKS) k_fused_c64
                 const int m = 1 << tpos;
                 const bool hi = (lane >> tpos) & 1;
                 if (cls == GC_HB) {
+                    // low lane: v + o; high lane: o - v, i.e. o + sg v with sg = -1
+                    const float sg = hi ? -1.f : 1.f;
 #pragma unroll
                     for (int j = 0; j < NA; ++j) {
                         const float2 o = shfl<float>(v[j], m);
-                        v[j] = hi ? make_float2(o.x - v[j].x, o.y - v[j].y) : make_float2(v[j].x + o.x, v[j].y + o.y);
+                        v[j] = make_float2(fmaf(sg, v[j].x, o.x), fmaf(sg, v[j].y, o.y));
                     }
                 } else if (cls == GC_X) {
 #pragma unroll
