@@ -281,6 +281,37 @@ def test_random_circuit_n30_full_size():
     assert abs(s128.prob(0) - 1) < 1e-10
 
 
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_qft_n30_closed_form_sampled(dtype):
+    # the fused passes at the throughput workload's size (n = 30, the bench's
+    # launch configuration: the default fused plan) on a circuit with a
+    # closed form: the QFT circuit of a basis state |x>, whose output
+    # amplitudes are 2^{-n/2} e^{2 pi i x y / 2^n}, checked on sampled y
+    n = 30
+    x = W.basis_index(30030, n)
+    s = qs.State(n, dtype).init_basis(x)
+    qs.Plan(n, dtype, W.qft_circuit(n)).execute(s)
+    r = W.rng(17)
+    ys = np.concatenate([[0, 1, (1 << n) - 1], r.integers(0, 1 << n, size=61)]).astype(np.int64)
+    got = s.tensor[torch.from_numpy(ys).to("cuda")].cpu().numpy().astype(np.complex128)
+    ph = ((x * ys) % (1 << n)).astype(np.float64) / float(1 << n)
+    want = np.exp(2j * np.pi * ph) / math.sqrt(1 << n)
+    # relative error of each sampled amplitude, held to the state bound (480
+    # gates, depth <= 500); with the error spread evenly over the amplitudes
+    # this is the relative 2-norm error
+    tol = 1e-12 if dtype == "c128" else 1e-5
+    assert np.max(np.abs(got - want)) * math.sqrt(1 << n) < tol, np.max(np.abs(got - want))
+    assert abs(s.norm() - 1) < (1e-12 if dtype == "c128" else 1e-5)
+
+
+def test_alu_peak_probe():
+    f32, f64 = qs.alu_peak("f32"), qs.alu_peak("f64")
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    # lane FMAs per second: at most 128 (single) per SM per clock at 2.1 GHz
+    assert 1e12 < f32 < sms * 128 * 2.2e9
+    assert 1e10 < f64 < f32
+
+
 def test_edge_cases():
     s = qs.State(4, "c128").init_basis(3)
     with pytest.raises(qs.QsimError):
