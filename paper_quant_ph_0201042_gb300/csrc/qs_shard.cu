@@ -95,12 +95,13 @@ qs_status pack_common(qs_state *s, int q, int value, void *buf, bool unpack) {
     if (reinterpret_cast<uintptr_t>(buf) % amp) return fail(QS_EINVAL, "buffer not aligned to an amplitude");
     const uint64_t half = uint64_t(1) << (s->n - 1);
     int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, unpack ? "shard unpack: device" : "shard pack: device");
     const uint64_t blocks = std::min<uint64_t>((half + 255) / 256, uint64_t(std::max(1, sms)) * 8);
     k_pack<<<unsigned(blocks), 256, 0, s->stream>>>(static_cast<const uint8_t *>(s->d), static_cast<uint8_t *>(buf),
                                                     half, s->n - 1 - q, uint64_t(value), amp, unpack);
-    const cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     return e == cudaSuccess ? QS_OK : cuda_fail(e, unpack ? "shard unpack" : "shard pack");
 }
 
