@@ -640,25 +640,46 @@ __global__ void __launch_bounds__(AF_THREADS, 2) k_adj_pass(cplx<R> *__restrict_
                 i0[j] = q;
                 i0[NQ + j] = q | B;
             }
-            // the run's leading exchange steps (C-NOT-like, on bit A) become
-            // the choice of which element of each pair on A loads as x
-            bool flip[NP];
+            // the run's leading exchange steps (C-NOT-like, on bit A or B)
+            // become the choice of which element of each quadruple loads into
+            // which place: perm holds, in 2-bit fields, the source element
+            // (a + 2b for the offset a A + b B) of each place
+            uint32_t perm[NQ];
 #pragma unroll
-            for (int j = 0; j < NP; ++j) flip[j] = false;
+            for (int j = 0; j < NQ; ++j) perm[j] = 0xE4u;   // place e <- element e
             const int pre = P.run_pre[r];
             for (int k = k0; k < k0 + pre; ++k) {
                 const AdjFOp<R> &os = sops[k];
                 if ((base & os.om) != os.ov) continue;
                 const uint32_t cm = os.cm, cv = os.cv;
+                const bool sb = os.tpos == t2;                // exchange on B, else on A
+                const int e1 = sb ? 2 : 1, f0 = sb ? 1 : 2;   // pairs (0, e1) and (f0, 3)
 #pragma unroll
-                for (int j = 0; j < NP; ++j) flip[j] ^= (i0[j] & cm) == cv;
+                for (int j = 0; j < NQ; ++j) {
+                    const uint32_t q = i0[j];
+                    const bool c0 = (q & cm) == cv, c1 = ((sb ? q | A : q | B) & cm) == cv;
+                    uint32_t x = perm[j];
+                    uint32_t d = (x ^ (x >> (2 * e1))) & (c0 ? 3u : 0u);
+                    x ^= d | (d << (2 * e1));
+                    d = ((x >> (2 * f0)) ^ (x >> 6)) & (c1 ? 3u : 0u);
+                    x ^= (d << (2 * f0)) | (d << 6);
+                    perm[j] = x;
+                }
             }
 #pragma unroll
-            for (int j = 0; j < NP; ++j) {
+            for (int j = 0; j < NQ; ++j) {
                 if (ok[j]) {
-                    const uint32_t ia = flip[j] ? i0[j] | A : i0[j], ib = ia ^ A;
-                    px[j] = sp[ia]; py[j] = sp[ib];
-                    lx[j] = sl[ia]; ly[j] = sl[ib];
+                    const uint32_t q = i0[j], x = perm[j];
+                    uint32_t off[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const uint32_t src = (x >> (2 * e)) & 3u;
+                        off[e] = ((src & 1u) ? A : 0u) | ((src & 2u) ? B : 0u);
+                    }
+                    px[j] = sp[q | off[0]]; py[j] = sp[q | off[1]];
+                    px[NQ + j] = sp[q | off[2]]; py[NQ + j] = sp[q | off[3]];
+                    lx[j] = sl[q | off[0]]; ly[j] = sl[q | off[1]];
+                    lx[NQ + j] = sl[q | off[2]]; ly[NQ + j] = sl[q | off[3]];
                 }
             }
             bool onB = false;   // the arrays hold the pairs of bit B
@@ -785,13 +806,24 @@ void schedule_runs(const std::vector<int> &idx, const std::vector<AdjStep> &step
     order.clear();
     runs.clear();
     int cur = -1, cur2 = -1, len = 0;
+    bool lead = true;   // the run holds exchange steps only so far
+    auto fits = [&](int k) {
+        const int b = hops[size_t(idx[size_t(k)])].bit;
+        return b == cur || b == cur2 || cur < 0 || cur2 < 0;
+    };
     while (order.size() < m) {
         int pick = -1;
+        // while the run is only exchanges: another exchange on one of its
+        // bits (the leading exchanges are folded into the run's load)
+        if (lead)
+            for (int k : ready)
+                if (steps[size_t(idx[size_t(k)])].cls == AC_X && fits(k)) { pick = k; break; }
         // a step on a bit the run already has, then one that opens a bit
-        for (int k : ready) {
-            const int b = hops[size_t(idx[size_t(k)])].bit;
-            if (diag[size_t(k)] || b == cur || b == cur2) { pick = k; break; }
-        }
+        if (pick < 0)
+            for (int k : ready) {
+                const int b = hops[size_t(idx[size_t(k)])].bit;
+                if (diag[size_t(k)] || b == cur || b == cur2) { pick = k; break; }
+            }
         if (pick < 0)
             for (int k : ready)
                 if (cur < 0 || cur2 < 0) { pick = k; break; }
@@ -799,8 +831,10 @@ void schedule_runs(const std::vector<int> &idx, const std::vector<AdjStep> &step
             runs.push_back({len, cur, cur2});
             cur = cur2 = -1;
             len = 0;
+            lead = true;
             continue;
         }
+        if (steps[size_t(idx[size_t(pick)])].cls != AC_X) lead = false;
         if (!diag[size_t(pick)]) {
             const int b = hops[size_t(idx[size_t(pick)])].bit;
             if (cur < 0) cur = b;
@@ -853,10 +887,11 @@ bool plan_sweep(int n, int K, const std::vector<AdjStep> &steps, const std::vect
                 std::find(sp.tile.begin(), sp.tile.end(), hops[size_t(j)].bit) == sp.tile.end())
                 return false;
         for (size_t r = 0, k = 0; r < sp.runs.size(); k += size_t(sp.runs[r].len), ++r) {
-            // leading exchanges on the run's first bit fold into the load
+            // leading exchanges on the run's bits fold into the load
             int pre = 0;
             while (pre < sp.runs[r].len && steps[size_t(sp.order[k + size_t(pre)])].cls == AC_X &&
-                   hops[size_t(sp.order[k + size_t(pre)])].bit == sp.runs[r].bit)
+                   (hops[size_t(sp.order[k + size_t(pre)])].bit == sp.runs[r].bit ||
+                    hops[size_t(sp.order[k + size_t(pre)])].bit == sp.runs[r].bit2))
                 ++pre;
             sp.pre.push_back(pre);
         }
