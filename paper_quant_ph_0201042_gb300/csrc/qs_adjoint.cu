@@ -244,7 +244,16 @@ int kind_angles(int kind) {
 // ---------------------------------------------------------------------------
 // Fused reverse sweep
 // ---------------------------------------------------------------------------
-constexpr int AF_THREADS = 256;
+// threads per CTA and resident CTAs per SM of the fused sweep (256 and 2
+// measured fastest on the n = 26 ansatz: 186 ms, against 206 ms for 512 and
+// 2 with 64 registers, 236 ms for 512 and 1)
+#ifndef QS_AF_THREADS
+#define QS_AF_THREADS 256
+#endif
+#ifndef QS_AF_MINB
+#define QS_AF_MINB 2
+#endif
+constexpr int AF_THREADS = QS_AF_THREADS;
 constexpr int AF_WARPS = AF_THREADS / 32;
 // at most ADJ_MAX_OPS steps per pass (the planner counts two budget units per op)
 constexpr int ADJ_MAX_OPS = 64;
@@ -570,14 +579,14 @@ __device__ __forceinline__ void tile_io(cplx<R> *__restrict__ psi, cplx<R> *__re
     }
 }
 
-// pairs per thread: tiles of 2^12 (complex64) or 2^11 (complex128) amplitudes
-template <typename R>
-constexpr int adj_np() { return sizeof(R) == 4 ? 8 : 4; }
+// tiles of 2^12 (complex64) or 2^11 (complex128) amplitudes; pairs per thread
 template <typename R>
 constexpr int adj_full_k() { return sizeof(R) == 4 ? 12 : 11; }
+template <typename R>
+constexpr int adj_np() { return (1 << (adj_full_k<R>() - 1)) / AF_THREADS; }
 
 template <typename R>
-__global__ void __launch_bounds__(AF_THREADS, 2) k_adj_pass(cplx<R> *__restrict__ psi, cplx<R> *__restrict__ lam,
+__global__ void __launch_bounds__(AF_THREADS, QS_AF_MINB) k_adj_pass(cplx<R> *__restrict__ psi, cplx<R> *__restrict__ lam,
                                                             const __grid_constant__ AdjFPass<R> P,
                                                             double *__restrict__ part) {
     constexpr int NP = adj_np<R>();
