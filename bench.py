@@ -55,12 +55,8 @@ def amp_updates(n, gates):
 
 def workload_config(args, n_ranks):
     n = args.n
-    if args.dtype == "c64":
-        kind = "complex64"
-    elif args.no_fuse or args.arith == "f64":
-        kind = "complex128 (double-precision instructions)"
-    else:
-        kind = "complex128 (double-single arithmetic)"
+    # the workload only (the arithmetic each arm uses is in the line's "arith")
+    kind = "complex64" if args.dtype == "c64" else "complex128"
     return {
         "workload": "random circuit n=%d, %d layers (Haar SU(2) on every qubit + C-NOTs on %d disjoint pairs), %s state"
                     % (n, LAYERS, n // 2, kind),
@@ -208,6 +204,7 @@ def run_reference(args, rank, world):
         "sample_ms_per_step": statistics.median([s["sample_seconds"] for s in steps]) * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic", "config": workload_config(args, world),
+        "arith": "FP64 (the CPU oracle: plain row-by-row gate application, OpenMP over rows)",
         "cpu_baseline": {"value": val, "unit": "amp-updates/s", "cores": base["cores"],
                          "kind": "oracle", "sample": base["sample"]},
         "e2e": {"value": val, "unit": "amp-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
