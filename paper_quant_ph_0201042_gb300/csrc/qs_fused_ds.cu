@@ -130,18 +130,24 @@ __device__ __forceinline__ uint32_t pair_index(uint32_t p, int t) {
     return ((p >> t) << (t + 1)) | (p & ((1u << t) - 1u));
 }
 
-// One 2x2 op of type TY on the thread's pairs whose controls hold.
-template <int TY>
+// One 2x2 op of type TY on the thread's pairs whose controls hold (CTL:
+// the op has controls on tile bits).  The thread's pair j is p = tid + j *
+// DTHREADS; with the zero inserted at bit t its index is the index of pair
+// tid ORed with that of j * DTHREADS (the two have no bit in common), so the
+// eight indices cost one OR each.
+template <int TY, bool CTL>
 __device__ __forceinline__ void pairs_loop(float4 *amp, int t, uint32_t tm, uint32_t tv, uint32_t xm, const float *c,
                                            int tid) {
     ccst u00{}, u01{}, u10{}, u11{};
     if (TY == D_GEN || TY == D_REAL) { u00 = cst(c); u01 = cst(c + 4); u10 = cst(c + 8); u11 = cst(c + 12); }
+    static_assert(DT / 2 / DTHREADS == 8, "eight pairs per thread");
+    const uint32_t ib = pair_index(uint32_t(tid), t), tb = 1u << t;
+    const uint32_t o1 = pair_index(DTHREADS, t), o2 = pair_index(2 * DTHREADS, t), o4 = pair_index(4 * DTHREADS, t);
 #pragma unroll DUNROLL
     for (int j = 0; j < DT / 2 / DTHREADS; ++j) {
-        const uint32_t p = uint32_t(tid + j * DTHREADS);
-        const uint32_t i0 = pair_index(p, t), i1 = i0 | (1u << t);
-        if ((i0 & tm) != tv) continue;
-        const uint32_t q0 = i0 ^ xm, q1 = i1 ^ xm;
+        const uint32_t i0 = ib | ((j & 1) ? o1 : 0u) | ((j & 2) ? o2 : 0u) | ((j & 4) ? o4 : 0u);
+        if (CTL && (i0 & tm) != tv) continue;
+        const uint32_t q0 = i0 ^ xm, q1 = q0 ^ tb;
         camp x = ld(amp[q0]), y = ld(amp[q1]);
         if (TY == D_X) {
             amp[q0] = st(y);
@@ -214,10 +220,16 @@ __global__ void __launch_bounds__(DTHREADS, DMINBLOCKS) k_fused_ds(double2 *__re
                     }
                 }
             } else {
-                if (type == D_GEN) pairs_loop<D_GEN>(amp, o.tbit, tm, tv, xm, o.c, tid);
-                else if (type == D_REAL) pairs_loop<D_REAL>(amp, o.tbit, tm, tv, xm, o.c, tid);
-                else if (type == D_HB) pairs_loop<D_HB>(amp, o.tbit, tm, tv, xm, o.c, tid);
-                else pairs_loop<D_X>(amp, o.tbit, tm, tv, xm, o.c, tid);
+                if (tm == 0) {
+                    if (type == D_GEN) pairs_loop<D_GEN, false>(amp, o.tbit, tm, tv, xm, o.c, tid);
+                    else if (type == D_REAL) pairs_loop<D_REAL, false>(amp, o.tbit, tm, tv, xm, o.c, tid);
+                    else pairs_loop<D_HB, false>(amp, o.tbit, tm, tv, xm, o.c, tid);   // (D_X without controls relabels)
+                } else {
+                    if (type == D_GEN) pairs_loop<D_GEN, true>(amp, o.tbit, tm, tv, xm, o.c, tid);
+                    else if (type == D_REAL) pairs_loop<D_REAL, true>(amp, o.tbit, tm, tv, xm, o.c, tid);
+                    else if (type == D_HB) pairs_loop<D_HB, true>(amp, o.tbit, tm, tv, xm, o.c, tid);
+                    else pairs_loop<D_X, true>(amp, o.tbit, tm, tv, xm, o.c, tid);
+                }
             }
             __syncthreads();
         }
