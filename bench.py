@@ -259,7 +259,7 @@ def rooflines(args, n, gates, kern_ms_step, launches_step, sm_mhz, sms, peaks):
     ngen = general_gates(gates)
     issue_peak = sms * 128 * sm_mhz * 1e6          # FP32 lanes x SM clock (instructions/s)
     fp64_flops = ngen * 16 * (1 << n)              # 8 double multiply-adds per amplitude
-    ds = args.dtype == "c128" and args.arith != "f64" and not args.no_fuse
+    ds = args.dtype == "c128" and args.arith != "f64"
     if ds:
         instr = ngen * DS_INSTR_GENERAL * (1 << n)
         views["alu"] = {"achieved": instr / t / 1e12, "peak": issue_peak / 1e12, "unit": "T FP32 instr/s",
@@ -287,7 +287,7 @@ def rooflines(args, n, gates, kern_ms_step, launches_step, sm_mhz, sms, peaks):
     bound = "alu" if t_alu > t_hbm else "hbm"
     main = views[bound]
     if args.no_fuse:
-        traffic, kern = None, "k_pair"
+        traffic, kern = None, "k_pair_ds" if ds else "k_pair"
     elif ds:
         traffic, kern = DS_TRAFFIC_N26 * (1 << (n - 26)), "k_fused_ds"
     elif args.dtype == "c64":
@@ -455,20 +455,36 @@ def secondary(args, torch, qs, state128, peaks, sms, sm_mhz):
         st.close()
     _release(torch)
 
-    # unfused per-gate path (one pair sweep per gate), complex128 with double
-    # instructions, on the first two layers of the n = 30 circuit
-    if state128 is not None:
-        pre = gates[:2 * (n + n // 2)]
-        pu = qs.Plan(n, "c128", pre, fuse=False)
-        run = lambda: pu.execute(state128)
-        ms = _time(torch, run)
-        ub = sum(2 * 16 * (1 << (n - len(g.controls))) for g in pre)
-        out["unfused_c128_n30"] = {"gates": len(pre), "ms": ms, "gates_per_s": len(pre) / (ms / 1e3),
-                                   "amp_updates_per_s": amp_updates(n, pre) / (ms / 1e3),
-                                   "hbm_gbs": ub / (ms / 1e3) / 1e9, "hbm_frac": ub / (ms / 1e3) / 1e9 / hbm_peak,
-                                   "note": "first 2 of 40 layers; one launch per gate, double-precision "
-                                           "instructions (FP64-pipe bound on this part)"}
+    # unfused per-gate path (one pair sweep per gate, the paper's evolution
+    # step as written) on the first two layers of the n = 30 circuit: every
+    # gate reads and writes the amplitudes it touches once, so the HBM
+    # fraction is the figure of merit
+    pre = gates[:2 * (n + n // 2)]
+    unf = {}
+    for name, dt_u, ar_u, B in (("c128_double_single", "c128", "default", 16), ("c128_f64", "c128", "f64", 16),
+                                ("c64", "c64", "default", 8)):
+        if dt_u == "c128" and state128 is None:
+            continue
+        su = state128 if dt_u == "c128" else qs.State(n, "c64")
+        pu = qs.Plan(n, dt_u, pre, fuse=False, arith=ar_u)
+        run = lambda: pu.execute(su)
+        run()
+        ms = _time(torch, run, reps=2 if name != "c128_f64" else 1)
+        ub = sum(2 * B * (1 << (n - len(g.controls))) for g in pre)
+        unf[name] = {"ms": ms, "gates_per_s": len(pre) / (ms / 1e3),
+                     "amp_updates_per_s": amp_updates(n, pre) / (ms / 1e3),
+                     "hbm_gbs": ub / (ms / 1e3) / 1e9, "hbm_frac": ub / (ms / 1e3) / 1e9 / hbm_peak}
         del pu
+        if su is not state128:
+            su.close()
+        _release(torch)
+    if unf:
+        unf["workload"] = ("first 2 of the 40 layers of the n=%d random circuit (%d gates), one pair-sweep launch "
+                           "per gate; bytes = one read and one write of the amplitudes each gate touches" % (n, len(pre)))
+        unf["arith"] = {"c128_double_single": "double-single (the default for complex128)",
+                        "c128_f64": "double-precision instructions (FP64-pipe bound on this part)",
+                        "c64": "FP32 instructions"}
+        out["unfused_n30"] = unf
 
     # the QFT black box (FFT, Sec. 2.3.2), complex64 n = 30: 4 transform
     # passes and a bit-reversal pass, each one read + one write
@@ -728,7 +744,7 @@ def main():
         "arith": ("double-single: each double split into two floats (48 significant bits), gates by "
                   "error-free products and sums on the FP32 pipe; state, copies and reductions in FP64; "
                   "parity vs the FP64 oracle <= 1e-12"
-                  if (args.dtype == "c128" and arith != "f64" and not args.no_fuse) else
+                  if (args.dtype == "c128" and arith != "f64") else
                   ("FP64 instructions" if args.dtype == "c128" else "FP32 instructions, FP64 reductions")),
         "data": "synthetic", "config": workload_config(args, world),
         "gates_per_s": world * len(gates) / (ms_per_step / 1e3),

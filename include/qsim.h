@@ -96,16 +96,17 @@ typedef struct {
  * (or NULL) selects the defaults. */
 typedef struct {
     int32_t no_fusion;       /* 1: one unfused pair-sweep launch per gate (the plain
-                                per-gate path, double-precision instructions for a
-                                complex128 state); 0: fuse runs of gates into tile passes */
+                                per-gate path); 0: fuse runs of gates into tile passes */
     int32_t max_ops_per_pass;/* 0: default */
-    int32_t c128_arith;      /* arithmetic of the fused passes over a complex128 state:
-                                QS_ARITH_DEFAULT (0) or QS_ARITH_DS: double-single (each
-                                double split into two floats carrying 48 significant bits;
-                                products and sums by error-free transformations on the
-                                single-precision pipe; the state stays complex128 in
-                                memory); QS_ARITH_F64: double-precision instructions.
-                                Double-single needs n >= 10, else the passes use doubles. */
+    int32_t c128_arith;      /* arithmetic of the passes or per-gate sweeps over a
+                                complex128 state: QS_ARITH_DEFAULT (0) or QS_ARITH_DS:
+                                double-single (each double split into two floats carrying
+                                48 significant bits; products and sums by error-free
+                                transformations on the single-precision pipe; the state
+                                stays complex128 in memory); QS_ARITH_F64:
+                                double-precision instructions.  Fused double-single passes
+                                need n >= 12 (2^12-amplitude tiles), else the passes use
+                                doubles; the per-gate sweeps have no minimum. */
     int32_t reserved[5];
 } qs_exec_opts;
 
@@ -141,6 +142,15 @@ qs_status qs_info(const qs_state *s, void **dev_ptr, int *n, qs_dtype *dt);
 /* --------------------------------------------------------------------- */
 /* Evolution steps, Sec. 2.2                                               */
 /* --------------------------------------------------------------------- */
+
+/* The single-gate calls below launch one pair sweep per gate.  A complex128
+ * state is updated in double-single arithmetic: each amplitude's doubles are
+ * split into float pairs carrying 48 significant bits, the update runs on the
+ * single-precision pipe by error-free products and sums, and the results are
+ * joined back into doubles (a relative error of a few 2^-48 per gate, against
+ * 2^-53 for double-precision instructions).  qs_apply_circuit with
+ * no_fusion = 1 and c128_arith = QS_ARITH_F64 runs the same sweeps with
+ * double-precision instructions. */
 
 /* |x>: amplitude x set to 1, all others to 0.  QS_ERANGE if x >= 2^n. */
 qs_status qs_init_basis(qs_state *s, uint64_t x);

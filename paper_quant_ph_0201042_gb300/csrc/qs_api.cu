@@ -223,7 +223,7 @@ qs_status qs_apply_gate(qs_state *s, const qs_gate *g) {
     HostOp op;
     qs_status st = synthesize(s->n, *g, op);
     if (st != QS_OK) return st;
-    cudaError_t e = launch_op(s, op);
+    cudaError_t e = launch_op(s, op, true);
     return e == cudaSuccess ? QS_OK : cuda_fail(e, "gate launch");
 }
 

@@ -236,6 +236,15 @@ QS_HD camp cmad2(const ccst &a, const camp &x, const ccst &b, const camp &y) {
     return o;
 }
 
+// a*x + b*y with real a, b (a.rh, a.rl and b.rh, b.rl; the imaginary parts
+// are ignored): each output component is a two-term dot product.
+QS_HD camp rmad2(const ccst &a, const camp &x, const ccst &b, const camp &y) {
+    camp o;
+    dot2(a.rh, a.rl, x.rh, x.rl, b.rh, b.rl, y.rh, y.rl, o.rh, o.rl);
+    dot2(a.rh, a.rl, x.ih, x.il, b.rh, b.rl, y.ih, y.il, o.ih, o.il);
+    return o;
+}
+
 // d*x (complex).
 QS_HD camp cmul(const ccst &d, const camp &x) {
     camp o;

@@ -878,6 +878,7 @@ struct Plan {
     int n = 0;
     qs_dtype dt = QS_C64;
     bool fused = false;
+    bool unfused_ds = false;                 // unfused mode: complex128 gates in double-single arithmetic
     DsPlan *dsp = nullptr;                   // complex128 passes in double-single arithmetic (qs_fused_ds.cu)
     std::vector<HostOp> ops;                 // unfused mode
     std::vector<PassDesc<float>> pf;         // fused passes, complex64
@@ -1472,6 +1473,7 @@ qs_status plan_build(int n, qs_dtype dt, const std::vector<HostOp> &ops, const q
     const bool ds = dt == QS_C128 && o.c128_arith != QS_ARITH_F64 && n >= ds_min_qubits();
     if (!P->fused) {
         P->ops = ops;
+        P->unfused_ds = dt == QS_C128 && o.c128_arith != QS_ARITH_F64;
     } else if (ds) {
         qs_status st = ds_plan_build(n, ops, o.max_ops_per_pass, temp, &P->dsp);
         if (st != QS_OK) {
@@ -1502,7 +1504,7 @@ qs_status plan_run(qs_state *s, Plan *p) {
         for (const HostOp &o : p->ops) {
             if (o.cls == GC_ID) continue;
             e = p->mark(s->stream, false);
-            if (e == cudaSuccess) e = launch_op(s, o);
+            if (e == cudaSuccess) e = launch_op(s, o, p->unfused_ds);
             if (e == cudaSuccess) e = p->mark(s->stream, true);
             if (e != cudaSuccess) break;
         }

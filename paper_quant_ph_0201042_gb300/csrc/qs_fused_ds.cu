@@ -100,22 +100,13 @@ __device__ __forceinline__ ccst cst(const float *c) { return {c[0], c[1], c[2], 
 __device__ __forceinline__ camp ld(const float4 &f) { return {f.x, f.y, f.z, f.w}; }
 __device__ __forceinline__ float4 st(const camp &a) { return make_float4(a.rh, a.rl, a.ih, a.il); }
 
-// a*x + b*y with real a, b (double-single): each output component is a
-// two-term dot product.
-__device__ __forceinline__ camp rmad2(const ccst &a, const camp &x, const ccst &b, const camp &y) {
-    camp o;
-    ds::dot2(a.rh, a.rl, x.rh, x.rl, b.rh, b.rl, y.rh, y.rl, o.rh, o.rl);
-    ds::dot2(a.rh, a.rl, x.ih, x.il, b.rh, b.rl, y.ih, y.il, o.ih, o.il);
-    return o;
-}
-
 // A 2x2 op (general, real or Hadamard butterfly) on the pair (x, y).
 __device__ __forceinline__ void pair_op(int type, const ccst &u00, const ccst &u01, const ccst &u10, const ccst &u11,
                                         camp &x, camp &y) {
     if (type == D_HB) {
         ds::butterfly(x, y);
     } else if (type == D_REAL) {
-        const camp nx = rmad2(u00, x, u01, y), ny = rmad2(u10, x, u11, y);
+        const camp nx = ds::rmad2(u00, x, u01, y), ny = ds::rmad2(u10, x, u11, y);
         x = nx;
         y = ny;
     } else {

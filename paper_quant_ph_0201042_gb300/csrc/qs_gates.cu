@@ -14,8 +14,17 @@
 // hold: the pair index is expanded into an amplitude index by inserting the
 // fixed bits (target and controls), so the work is 2^(n-1-#controls) pairs
 // and a gate with n-1 controls (Grover's phase oracle) touches one pair.
+//
+// A complex128 state is updated either with double-precision instructions
+// or, by default, in double-single arithmetic (qs_ds.cuh): each loaded double
+// is split into two floats, the pair update runs on the single-precision pipe
+// by error-free transformations, and the results are joined back into
+// doubles.  On this part the double pipe is too slow for a sweep to keep up
+// with HBM (8 double FMAs per amplitude); the double-single sweep is bound by
+// HBM instead.
 #include <algorithm>
 
+#include "qs_ds.cuh"
 #include "qs_internal.cuh"
 
 namespace qs {
@@ -90,6 +99,57 @@ __global__ void __launch_bounds__(THREADS) k_pair(cplx<R> *__restrict__ a, uint6
     }
 }
 
+// The same pair update on a complex128 state in double-single arithmetic.
+struct MatDS {
+    ds::ccst u00, u01, u10, u11;
+};
+
+__device__ __forceinline__ ds::camp ld_ds(const double2 &d) { return ds::load(d.x, d.y); }
+__device__ __forceinline__ double2 st_ds(const ds::camp &c) {
+    return make_double2(ds::join(c.rh, c.rl), ds::join(c.ih, c.il));
+}
+
+template <int CLS>
+__global__ void __launch_bounds__(THREADS) k_pair_ds(double2 *__restrict__ a, uint64_t count, uint64_t tbit,
+                                                     const __grid_constant__ Fixed f, const MatDS m) {
+    const uint64_t stride = uint64_t(gridDim.x) * THREADS;
+    for (uint64_t base = uint64_t(blockIdx.x) * THREADS + threadIdx.x; base < count;
+         base += stride * UNROLL) {
+        uint64_t i0[UNROLL];
+        double2 x[UNROLL], y[UNROLL];
+#pragma unroll
+        for (int k = 0; k < UNROLL; ++k) {
+            const uint64_t p = base + k * stride;
+            i0[k] = p < count ? deposit(p, f) : ~uint64_t(0);
+            if (p < count) {
+                x[k] = a[i0[k]];
+                y[k] = a[i0[k] | tbit];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < UNROLL; ++k) {
+            if (i0[k] == ~uint64_t(0)) continue;
+            const ds::camp X = ld_ds(x[k]), Y = ld_ds(y[k]);
+            ds::camp nx, ny;
+            if (CLS == GC_GEN) {
+                nx = ds::cmad2(m.u00, X, m.u01, Y);
+                ny = ds::cmad2(m.u10, X, m.u11, Y);
+            } else if (CLS == GC_REAL) {
+                nx = ds::rmad2(m.u00, X, m.u01, Y);
+                ny = ds::rmad2(m.u10, X, m.u11, Y);
+            } else if (CLS == GC_DIAG) {
+                nx = ds::cmul(m.u00, X);
+                ny = ds::cmul(m.u11, Y);
+            } else {  // GC_ANTI
+                nx = ds::cmul(m.u01, Y);
+                ny = ds::cmul(m.u10, X);
+            }
+            a[i0[k]] = st_ds(nx);
+            a[i0[k] | tbit] = st_ds(ny);
+        }
+    }
+}
+
 // One phase on the amplitudes of one pattern (GC_PHASE): only those are read
 // and written.
 template <typename R>
@@ -110,6 +170,25 @@ __global__ void __launch_bounds__(THREADS) k_phase(cplx<R> *__restrict__ a, uint
 #pragma unroll
         for (int k = 0; k < UNROLL; ++k)
             if (i[k] != ~uint64_t(0)) a[i[k]] = cmul<R>(d, x[k]);
+    }
+}
+
+__global__ void __launch_bounds__(THREADS) k_phase_ds(double2 *__restrict__ a, uint64_t count,
+                                                      const __grid_constant__ Fixed f, ds::ccst d) {
+    const uint64_t stride = uint64_t(gridDim.x) * THREADS;
+    for (uint64_t base = uint64_t(blockIdx.x) * THREADS + threadIdx.x; base < count;
+         base += stride * UNROLL) {
+        uint64_t i[UNROLL];
+        double2 x[UNROLL];
+#pragma unroll
+        for (int k = 0; k < UNROLL; ++k) {
+            const uint64_t p = base + k * stride;
+            i[k] = p < count ? deposit(p, f) : ~uint64_t(0);
+            if (p < count) x[k] = a[i[k]];
+        }
+#pragma unroll
+        for (int k = 0; k < UNROLL; ++k)
+            if (i[k] != ~uint64_t(0)) a[i[k]] = st_ds(ds::cmul(d, ld_ds(x[k])));
     }
 }
 
@@ -179,8 +258,20 @@ Mat<R> to_mat(const double *u) {
     return m;
 }
 
+ds::ccst split_c(double re, double im) {
+    ds::ccst c;
+    ds::split_const(re, c.rh, c.rl);
+    ds::split_const(im, c.ih, c.il);
+    return c;
+}
+
+MatDS to_mat_ds(const double *u) {
+    return {split_c(u[0], u[1]), split_c(u[2], u[3]), split_c(u[4], u[5]), split_c(u[6], u[7])};
+}
+
+// DS: complex128 arithmetic in double-single (ignored for complex64).
 template <typename R>
-cudaError_t launch_op_t(qs_state *s, const HostOp &op) {
+cudaError_t launch_op_t(qs_state *s, const HostOp &op, bool DS) {
     cplx<R> *a = static_cast<cplx<R> *>(s->d);
     const int n = s->n;
     const int nctrl = __builtin_popcountll(op.cmask);
@@ -201,14 +292,30 @@ cudaError_t launch_op_t(qs_state *s, const HostOp &op) {
         const uint64_t v = op.cval | (op.phase_on ? (uint64_t(1) << op.bit) : 0);
         Fixed f = make_fixed(pos, v);
         const double *d = op.phase_on ? &op.u[6] : &op.u[0];
-        k_phase<R><<<grid_for(count), THREADS, 0, s->stream>>>(a, count, f, mk<R>(R(d[0]), R(d[1])));
+        if (DS && sizeof(R) == 8)
+            k_phase_ds<<<grid_for(count), THREADS, 0, s->stream>>>(reinterpret_cast<double2 *>(a), count, f,
+                                                                  split_c(d[0], d[1]));
+        else
+            k_phase<R><<<grid_for(count), THREADS, 0, s->stream>>>(a, count, f, mk<R>(R(d[0]), R(d[1])));
         return cudaGetLastError();
     }
     const uint64_t count = uint64_t(1) << (n - 1 - nctrl);
     Fixed f = make_fixed(pos, op.cval);
     const uint64_t tbit = uint64_t(1) << op.bit;
-    Mat<R> m = to_mat<R>(op.u);
     const unsigned g = grid_for(count);
+    if (DS && sizeof(R) == 8 && op.cls != GC_X) {
+        double2 *ad = reinterpret_cast<double2 *>(a);
+        const MatDS md = to_mat_ds(op.u);
+        switch (op.cls) {
+        case GC_GEN: k_pair_ds<GC_GEN><<<g, THREADS, 0, s->stream>>>(ad, count, tbit, f, md); break;
+        case GC_REAL: k_pair_ds<GC_REAL><<<g, THREADS, 0, s->stream>>>(ad, count, tbit, f, md); break;
+        case GC_DIAG: k_pair_ds<GC_DIAG><<<g, THREADS, 0, s->stream>>>(ad, count, tbit, f, md); break;
+        case GC_ANTI: k_pair_ds<GC_ANTI><<<g, THREADS, 0, s->stream>>>(ad, count, tbit, f, md); break;
+        default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
+    Mat<R> m = to_mat<R>(op.u);
     switch (op.cls) {
     case GC_GEN: k_pair<R, GC_GEN><<<g, THREADS, 0, s->stream>>>(a, count, tbit, f, m); break;
     case GC_REAL: k_pair<R, GC_REAL><<<g, THREADS, 0, s->stream>>>(a, count, tbit, f, m); break;
@@ -222,8 +329,8 @@ cudaError_t launch_op_t(qs_state *s, const HostOp &op) {
 
 }  // namespace
 
-cudaError_t launch_op(qs_state *s, const HostOp &op) {
-    return s->dt == QS_C64 ? launch_op_t<float>(s, op) : launch_op_t<double>(s, op);
+cudaError_t launch_op(qs_state *s, const HostOp &op, bool ds) {
+    return s->dt == QS_C64 ? launch_op_t<float>(s, op, false) : launch_op_t<double>(s, op, ds);
 }
 
 cudaError_t launch_init_basis(qs_state *s, uint64_t x) {

@@ -133,7 +133,9 @@ qs_status cuda_fail(cudaError_t e, const char *where);
 qs_status synthesize(int n, const qs_gate &g, HostOp &op);
 
 // Unfused kernels (qs_gates.cu).
-cudaError_t launch_op(qs_state *s, const HostOp &op);
+// One unfused gate launch; ds: a complex128 state in double-single arithmetic
+// (else double-precision instructions).
+cudaError_t launch_op(qs_state *s, const HostOp &op, bool ds);
 cudaError_t launch_init_basis(qs_state *s, uint64_t x);
 
 // Reductions (qs_reduce.cu). Results are written to s->result on the device.

@@ -65,6 +65,18 @@ def test_unfused_gates_every_kind(dtype, n):
     assert err(got, want) < TOL[dtype]
 
 
+@pytest.mark.parametrize("arith", ["default", "f64"])
+@pytest.mark.parametrize("n", [2, 7, 12])
+def test_unfused_circuit_complex128_arithmetic(arith, n):
+    # the per-gate sweeps of a complex128 state in double-single (default) and
+    # in double-precision instructions, every gate kind, against the oracle
+    r = W.rng(3000 + n)
+    gates = [random_gate(r, n) for _ in range(80)]
+    psi = random_state(r, n)
+    want = oracle.run(n, gates, psi=psi)
+    assert err(gpu_run(n, gates, "c128", fuse=False, psi=psi, arith=arith), want) < TOL["c128"]
+
+
 @pytest.mark.parametrize("dtype", DTYPES)
 def test_entry_points(dtype):
     n = 9
