@@ -524,9 +524,11 @@ qs_status qs_sync(qs_state *s);
 /* Measured rate of fused multiply-add instructions on the current device,
  * in lane operations per second (kind 0: single precision, kind 1: double
  * precision): a kernel of sixteen independent FMA chains per thread on eight
- * 256-thread CTAs per SM, timed with CUDA events after a warm-up launch.
- * These are the denominators of the arithmetic rooflines.  Synchronous;
- * allocates and frees a small sink buffer.  Changes no device setting. */
+ * 256-thread CTAs per SM on a stream of its own, the best of five launches
+ * timed with CUDA events after about 200 ms of the same launches (so that
+ * the SM clock has left its idle level).  These are the denominators of the
+ * arithmetic rooflines.  Synchronous; allocates and frees a small sink
+ * buffer and a stream.  Changes no device setting. */
 qs_status qs_alu_peak(int kind, double *fma_per_s);
 
 /* Thread-local message describing the last failure of this thread. */

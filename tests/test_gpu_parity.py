@@ -319,8 +319,9 @@ def test_qft_n30_closed_form_sampled(dtype):
 def test_alu_peak_probe():
     f32, f64 = qs.alu_peak("f32"), qs.alu_peak("f64")
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    # lane FMAs per second: at most 128 (single) per SM per clock at 2.1 GHz
-    assert 1e12 < f32 < sms * 128 * 2.2e9
+    # lane FMAs per second: at most 128 (single) per SM per clock at 2.1 GHz,
+    # and at least half of that at a 1 GHz clock (the probe warms the clock up)
+    assert sms * 64 * 1e9 < f32 < sms * 128 * 2.2e9
     assert 1e10 < f64 < f32
 
 
