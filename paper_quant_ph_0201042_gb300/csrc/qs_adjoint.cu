@@ -593,6 +593,11 @@ __global__ void __launch_bounds__(AF_THREADS, QS_AF_MINB) k_adj_pass(cplx<R> *__
     extern __shared__ __align__(16) unsigned char smraw[];
     const int K = P.K;
     const uint32_t T = 1u << K;
+    // quadruples per thread that hold tile elements: the tile has T / 4
+    // quadruples, a whole number of CTA-wide rows of them (K >= the tile bits
+    // of one row, which the host guarantees), so the count is the same for
+    // every thread and the tests on it do not diverge
+    const int nqv = int(T / 4 / AF_THREADS);
     cplx<R> *sp = reinterpret_cast<cplx<R> *>(smraw);
     cplx<R> *sl = sp + T;
     Acc<R> *sacc = reinterpret_cast<Acc<R> *>(sl + T);                        // nacc x AF_WARPS
@@ -645,7 +650,7 @@ __global__ void __launch_bounds__(AF_THREADS, QS_AF_MINB) k_adj_pass(cplx<R> *__
                 const uint32_t p = tid + uint32_t(j) * AF_THREADS;
                 const uint32_t x = ((p >> lo) << (lo + 1)) | (p & ((1u << lo) - 1u));
                 const uint32_t q = ((x >> hi) << (hi + 1)) | (x & ((1u << hi) - 1u));
-                ok[j] = ok[NQ + j] = p < T / 4;
+                ok[j] = ok[NQ + j] = j < nqv;
                 i0[j] = q;
                 i0[NQ + j] = q | B;
             }
@@ -1115,7 +1120,7 @@ qs_status run_adjoint(qs_state *s, const std::vector<qs_gate> &gg, size_t n_para
     // fused sweep: tiles of 2^K amplitudes (64 KiB per vector), one CTA per
     // tile at a time, as many CTAs as fit
     const int Kf = std::min(n, adj_full_k<R>());
-    const bool fused = fuse && n >= 6;
+    const bool fused = fuse && (size_t(1) << Kf) >= size_t(4) * AF_THREADS;   // a tile of at least one row of quadruples per thread
     int nblk = RED_BLOCKS;
     if (fused) {
         // the largest pass: ADJ_MAX_OPS steps with two generators each
