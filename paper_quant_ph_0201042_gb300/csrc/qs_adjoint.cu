@@ -459,7 +459,8 @@ __device__ __forceinline__ void diag_elem_im(cplx<R> d, R g, cplx<R> &x, cplx<R>
 
 // DK: where the diagonal's bit lies.  0: the run's own bit (the pair's
 // elements take d0 and d1); 1: an outer bit (one entry for the whole tile);
-// 2: another tile bit (one entry per pair).
+// 2: another tile bit (one entry per pair); 3: the run's other bit (the
+// first half of the pair arrays has it clear, the second half set).
 template <typename R, int NP, int NA, bool CHK, int DK, bool IM>
 __device__ __forceinline__ void run_diag(const AdjFOp<R> &os, bool outer_one, uint32_t tb, const bool (&ok)[NP],
                                          const uint32_t (&i0)[NP], cplx<R> (&px)[NP], cplx<R> (&py)[NP],
@@ -477,8 +478,8 @@ __device__ __forceinline__ void run_diag(const AdjFOp<R> &os, bool outer_one, ui
         const uint32_t e0 = i0[j], e1 = i0[j] | tb;
         cplx<R> da = d0, db = d1, ga = g0, gb = g3, ha = h0, hb = h3;
         if (DK == 1) { db = d0; gb = g0; hb = h0; }
-        if (DK == 2) {
-            const bool one = (e0 >> tpos) & 1;
+        if (DK == 2 || DK == 3) {
+            const bool one = DK == 3 ? j >= NP / 2 : ((e0 >> tpos) & 1) != 0;
             da = db = one ? d1 : d0;
             if (NA > 0) ga = gb = one ? g3 : g0;
             if (NA > 1) ha = hb = one ? h3 : h0;
@@ -494,21 +495,24 @@ __device__ __forceinline__ void run_diag(const AdjFOp<R> &os, bool outer_one, ui
 }
 
 template <typename R, int NP, int NA, bool CHK, bool IM>
-__device__ __forceinline__ void run_diag_any(const AdjFOp<R> &os, uint64_t base, uint32_t tb, const bool (&ok)[NP],
-                                             const uint32_t (&i0)[NP], cplx<R> (&px)[NP], cplx<R> (&py)[NP],
-                                             cplx<R> (&lx)[NP], cplx<R> (&ly)[NP], R &a0, R &a1) {
+__device__ __forceinline__ void run_diag_any(const AdjFOp<R> &os, uint64_t base, uint32_t tb, uint32_t ob,
+                                             const bool (&ok)[NP], const uint32_t (&i0)[NP], cplx<R> (&px)[NP],
+                                             cplx<R> (&py)[NP], cplx<R> (&lx)[NP], cplx<R> (&ly)[NP], R &a0, R &a1) {
     if (os.mode == 3) {
         const bool outer_one = (base >> os.tpos) & 1;
         run_diag<R, NP, NA, CHK, 1, IM>(os, outer_one, tb, ok, i0, px, py, lx, ly, a0, a1);
     } else if ((1u << os.tpos) == tb) {
         run_diag<R, NP, NA, CHK, 0, IM>(os, false, tb, ok, i0, px, py, lx, ly, a0, a1);
+    } else if ((1u << os.tpos) == ob) {
+        run_diag<R, NP, NA, CHK, 3, IM>(os, false, tb, ok, i0, px, py, lx, ly, a0, a1);
     } else {
         run_diag<R, NP, NA, CHK, 2, IM>(os, false, tb, ok, i0, px, py, lx, ly, a0, a1);
     }
 }
 
 template <typename R, int NP, bool CHK>
-__device__ __forceinline__ void step_on_pairs(const AdjFOp<R> &os, uint64_t base, uint32_t tb, const bool (&ok)[NP],
+__device__ __forceinline__ void step_on_pairs(const AdjFOp<R> &os, uint64_t base, uint32_t tb, uint32_t ob,
+                                              const bool (&ok)[NP],
                                               const uint32_t (&i0)[NP], cplx<R> (&px)[NP], cplx<R> (&py)[NP],
                                               cplx<R> (&lx)[NP], cplx<R> (&ly)[NP], R &a0, R &a1) {
     const int mode = os.mode, nang = os.nang;
@@ -524,10 +528,10 @@ __device__ __forceinline__ void step_on_pairs(const AdjFOp<R> &os, uint64_t base
         else if (nang == 1) run_pair<R, NP, 1, CHK>(os, ok, i0, px, py, lx, ly, a0, a1);
         else run_pair<R, NP, 2, CHK>(os, ok, i0, px, py, lx, ly, a0, a1);
     } else {
-        if (os.gk == 2) run_diag_any<R, NP, 1, CHK, true>(os, base, tb, ok, i0, px, py, lx, ly, a0, a1);
-        else if (nang == 0) run_diag_any<R, NP, 0, CHK, false>(os, base, tb, ok, i0, px, py, lx, ly, a0, a1);
-        else if (nang == 1) run_diag_any<R, NP, 1, CHK, false>(os, base, tb, ok, i0, px, py, lx, ly, a0, a1);
-        else run_diag_any<R, NP, 2, CHK, false>(os, base, tb, ok, i0, px, py, lx, ly, a0, a1);
+        if (os.gk == 2) run_diag_any<R, NP, 1, CHK, true>(os, base, tb, ob, ok, i0, px, py, lx, ly, a0, a1);
+        else if (nang == 0) run_diag_any<R, NP, 0, CHK, false>(os, base, tb, ob, ok, i0, px, py, lx, ly, a0, a1);
+        else if (nang == 1) run_diag_any<R, NP, 1, CHK, false>(os, base, tb, ob, ok, i0, px, py, lx, ly, a0, a1);
+        else run_diag_any<R, NP, 2, CHK, false>(os, base, tb, ob, ok, i0, px, py, lx, ly, a0, a1);
     }
 }
 
@@ -713,11 +717,11 @@ __global__ void __launch_bounds__(AF_THREADS, QS_AF_MINB) k_adj_pass(cplx<R> *__
                     }
                     onB = wantB;
                 }
-                const uint32_t tbv = onB ? B : A;
+                const uint32_t tbv = onB ? B : A, obv = onB ? A : B;
                 const int nang = os.nang;
                 R a0 = R(0), a1 = R(0);
-                if (os.cm == 0) step_on_pairs<R, NP, false>(os, base, tbv, ok, i0, px, py, lx, ly, a0, a1);
-                else step_on_pairs<R, NP, true>(os, base, tbv, ok, i0, px, py, lx, ly, a0, a1);
+                if (os.cm == 0) step_on_pairs<R, NP, false>(os, base, tbv, obv, ok, i0, px, py, lx, ly, a0, a1);
+                else step_on_pairs<R, NP, true>(os, base, tbv, obv, ok, i0, px, py, lx, ly, a0, a1);
                 if (nang > 0) {
                     const R s0 = warp_sum<R>(a0);
                     if (lane == 0) acc_add<R>(sacc[os.acc * AF_WARPS + warp], s0);

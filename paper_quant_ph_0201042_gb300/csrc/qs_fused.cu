@@ -527,11 +527,21 @@ __device__ __forceinline__ void s_hb(float2 (&v)[NA], uint32_t xm) {
 
 template <int T, int NA>
 __device__ __forceinline__ void s_diag(float2 (&v)[NA], float2 d0, float2 d1, uint32_t xm, int rm, int rv) {
+    // register j holds logical index j ^ xm: its entry is d0 or d1 by bit T
+    // of j, the two swapped where xm has bit T (the same across the warp, so
+    // a branch here and a compile-time choice per register)
+    if ((xm >> T) & 1) {
+        const float2 t = d0;
+        d0 = d1;
+        d1 = t;
+    }
+    if (rm == 0) {
 #pragma unroll
-    for (int j = 0; j < NA; ++j) {
-        const uint32_t l = uint32_t(j) ^ xm;
-        const float2 d = ((l >> T) & 1) ? d1 : d0;
-        if ((l & uint32_t(rm)) == uint32_t(rv)) v[j] = cmul<float>(d, v[j]);
+        for (int j = 0; j < NA; ++j) v[j] = cmul<float>(((j >> T) & 1) ? d1 : d0, v[j]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < NA; ++j)
+            if (lpred(j, xm, rm, rv)) v[j] = cmul<float>(((j >> T) & 1) ? d1 : d0, v[j]);
     }
 }
 
@@ -801,9 +811,14 @@ __global__ void __launch_bounds__(32 << QS_WB64, QS_FUSED_MINBLOCKS) k_fused_c64
                     const uint64_t word = tsel == 1 ? uint64_t(tl) : base;
                     const float2 d = ((word >> tpos) & 1) ? d1 : d0;
                     if (d.x == 1.f && d.y == 0.f) continue;   // this thread's entry is exactly 1
+                    if (rm == 0) {
 #pragma unroll
-                    for (int j = 0; j < NA; ++j)
-                        if (lpred(j, xm, rm, rv2)) v[j] = cmul<float>(d, v[j]);
+                        for (int j = 0; j < NA; ++j) v[j] = cmul<float>(d, v[j]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < NA; ++j)
+                            if (lpred(j, xm, rm, rv2)) v[j] = cmul<float>(d, v[j]);
+                    }
                 }
             }
         }
