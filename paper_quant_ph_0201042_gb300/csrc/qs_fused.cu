@@ -393,7 +393,8 @@ struct alignas(16) POp {
     uint8_t rmask, rval;
     uint8_t fast;          // state-vector fast paths: 1 uncontrolled general gate on a register slot,
                            // 2 X deferred into the index mask, 3 uncontrolled general gate on a lane bit,
-                           // 4 / 5 as 1 / 3 for a real matrix (RY, U_R, ...)
+                           // 4 / 5 as 1 / 3 for a real matrix (RY, U_R, ...), 6 / 7 an uncontrolled
+                           // Hadamard butterfly on a register slot / lane bit
     uint8_t pad0;
     uint32_t pad1;
     uint16_t tmask, tval;
@@ -662,7 +663,7 @@ __global__ void __launch_bounds__(32 << QS_WB64, QS_FUSED_MINBLOCKS) k_fused_c64
             // record; the deferred C-NOT path is skipped there (its control
             // values change with the trajectory's Pauli frame)
             int fast = int((hd.y >> 16) & 0xff);
-            if (TRAJ && fast == 2) fast = 0;
+            if (TRAJ && (fast == 2 || fast >= 6)) fast = 0;
             if (TRAJ && fast >= 4) fast = fast == 4 ? 1 : 3;   // a trajectory's matrix need not be real
             if (fast) {
                 // the common cases without the general dispatch: no predicate
@@ -674,6 +675,24 @@ __global__ void __launch_bounds__(32 << QS_WB64, QS_FUSED_MINBLOCKS) k_fused_c64
                     const uint64_t oval = uint64_t(oc.z) | (uint64_t(oc.w) << 32);
                     const bool ok = ((tl & (hd.w & 0xffff)) == (hd.w >> 16)) && ((base & omask) == oval);
                     xm ^= ok ? (1u << tp) : 0u;
+                    continue;
+                }
+                if (fast == 6) {   // Hadamard butterfly on a register slot (factor folded into the pass scale)
+                    if (tp == 0) s_hb<0, NA>(v, xm);
+                    else if (tp == 1) s_hb<1, NA>(v, xm);
+                    else if (tp == 2) s_hb<2, NA>(v, xm);
+                    else if (tp == 3) s_hb<3, NA>(v, xm);
+                    else s_hb<(RB64 > 4 ? 4 : 0), NA>(v, xm);
+                    continue;
+                }
+                if (fast == 7) {   // Hadamard butterfly on a lane bit: low lane v + o, high lane o - v
+                    const int m = 1 << tp;
+                    const float sg = ((lane >> tp) & 1) ? -1.f : 1.f;
+#pragma unroll
+                    for (int j = 0; j < NA; ++j) {
+                        const float2 o = shfl<float>(v[j], m);
+                        v[j] = make_float2(fmaf(sg, v[j].x, o.x), fmaf(sg, v[j].y, o.y));
+                    }
                     continue;
                 }
                 const float4 *cs4 = TRAJ ? reinterpret_cast<const float4 *>(srec[k].u) : reinterpret_cast<const float4 *>(q) + 2;
@@ -1386,7 +1405,11 @@ void convert_c64(const PassDesc<float> &D, const std::vector<FOp<float>> &ops, P
                  f.omask == 0)
             q.fast = 3;
         if ((q.fast == 1 || q.fast == 3) && f.u[1] == 0 && f.u[3] == 0 && f.u[5] == 0 && f.u[7] == 0)
-            q.fast = uint8_t(q.fast + 3);   // real matrix
+            q.fast = uint8_t(q.fast == 1 ? 4 : 5);   // real matrix
+        if (f.cls == GC_HB && f.rmask == 0 && f.tmask == 0 && f.omask == 0) {
+            if (f.type == OP_REG) q.fast = 6;
+            else if (f.type == OP_LANE) q.fast = 7;
+        }
         if (f.type == OP_XPOSE) {
             // position of each high tile bit in the old tile order
             // (register index bits above the warp bits, warp bits above the lanes)
