@@ -26,10 +26,11 @@
 // dU_j U_j^dagger).  A CTA loads the tile of psi and of lambda into shared
 // memory once, runs the pass's steps on it (gradient partial, then the
 // uncompute) and writes both tiles back: one HBM round trip of the two vectors
-// per pass instead of per step.  Within the tile the steps run in runs that
-// share one target bit (diagonal steps join any run): each thread keeps its
-// pairs of both vectors in registers for a whole run.
+// per pass instead of per step.  Within the tile the steps run in runs on up
+// to three target bits (diagonal steps join any run): each thread keeps
+// octets of both vectors in registers for a whole run.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <set>
@@ -270,15 +271,16 @@ struct alignas(16) AdjFOp {    // one reverse step of a pass, tile-local form
     int32_t slot0, slot1;      // global partial-sum slots of the generators
     int32_t gk;                // one generator of a special form: 1 real antisymmetric [[0, -g], [g, 0]]
                                // (mode 4), 2 imaginary diagonal diag(i a, i b) (modes 2, 3); else 0
-    int32_t pad_[3];
+    int32_t role;              // the run role (0, 1, 2) of the target bit; 3: a diagonal whose bit is no role
+    int32_t pad_[2];
     cplx<R> ui[4];             // U^dagger
     cplx<R> g0[4], g1[4];      // generators dU U^dagger
 };
 
-// A pass's steps come in runs: within a run every non-diagonal step has the
-// same tile-local target bit, so each thread keeps the same amplitude pairs
-// (psi and lambda, split on that bit) in registers for the whole run and the
-// tile goes through shared memory once per run instead of once per step.
+// A pass's steps come in runs: within a run every non-diagonal step targets
+// one of at most three tile bits (the run's roles), so each thread keeps the
+// same octets of psi and lambda in registers for the whole run and the tile
+// goes through shared memory once per run instead of once per step.
 template <typename R>
 struct AdjFPass {
     const AdjFOp<R> *ops;
@@ -287,7 +289,8 @@ struct AdjFPass {
     uint8_t tile_pos[16];
     uint8_t run_len[ADJ_MAX_OPS];
     uint8_t run_bit[ADJ_MAX_OPS];
-    uint8_t run_bit2[ADJ_MAX_OPS];   // second target bit of a two-bit run, 0xff for one bit
+    uint8_t run_bit2[ADJ_MAX_OPS];   // tile bits of roles 1 and 2 (other tile bits where the run has
+    uint8_t run_bit3[ADJ_MAX_OPS];   // fewer target bits)
     uint8_t run_pre[ADJ_MAX_OPS];    // leading exchange steps of the run, applied at its load
 };
 
@@ -361,85 +364,13 @@ __device__ __forceinline__ void cswap_ip(bool p, cplx<R> &x, cplx<R> &y) {
     memcpy(&y.x, &yr, sizeof(B)); memcpy(&y.y, &yi, sizeof(B));
 }
 
-// One step of a run on the thread's register pairs.  Pair steps act on the
-// run's bit (their controls exclude it); a diagonal step scales each element
-// by the entry its own target bit selects.  NA generators are accumulated.
-template <typename R, int NP, bool CHK>
-__device__ __forceinline__ void run_exchange(uint32_t cm, uint32_t cv, const bool (&ok)[NP], const uint32_t (&i0)[NP],
-                                             cplx<R> (&px)[NP], cplx<R> (&py)[NP], cplx<R> (&lx)[NP],
-                                             cplx<R> (&ly)[NP]) {
-#pragma unroll
-    for (int j = 0; j < NP; ++j) {
-        const bool p = ok[j] && (!CHK || (i0[j] & cm) == cv);
-        cswap_ip<R>(p, px[j], py[j]);
-        cswap_ip<R>(p, lx[j], ly[j]);
-    }
-}
-
-template <typename R, int NP, int NA, bool CHK>
-__device__ __forceinline__ void run_pair(const AdjFOp<R> &os, const bool (&ok)[NP], const uint32_t (&i0)[NP],
-                                         cplx<R> (&px)[NP], cplx<R> (&py)[NP], cplx<R> (&lx)[NP],
-                                         cplx<R> (&ly)[NP], R &a0, R &a1) {
-    const uint32_t cm = os.cm, cv = os.cv;
-    const cplx<R> u0 = os.ui[0], u1 = os.ui[1], u2 = os.ui[2], u3 = os.ui[3];
-    cplx<R> g[4], h[4];
-    if (NA > 0) for (int e = 0; e < 4; ++e) g[e] = os.g0[e];
-    if (NA > 1) for (int e = 0; e < 4; ++e) h[e] = os.g1[e];
-#pragma unroll
-    for (int j = 0; j < NP; ++j) {
-        if (!ok[j] || (CHK && (i0[j] & cm) != cv)) continue;
-        if (NA > 0) a0 += pair_grad<R>(g, px[j], py[j], lx[j], ly[j]);
-        if (NA > 1) a1 += pair_grad<R>(h, px[j], py[j], lx[j], ly[j]);
-        cmad_ip<R>(u0, u1, u2, u3, px[j], py[j]);
-        cmad_ip<R>(u0, u1, u2, u3, lx[j], ly[j]);
-    }
-}
-
-// real U^dagger and real generators: Re<l|g x> = g Re(conj(l) x) term by term
-template <typename R, int NP, int NA, bool CHK>
-__device__ __forceinline__ void run_pair_real(const AdjFOp<R> &os, const bool (&ok)[NP], const uint32_t (&i0)[NP],
-                                              cplx<R> (&px)[NP], cplx<R> (&py)[NP], cplx<R> (&lx)[NP],
-                                              cplx<R> (&ly)[NP], R &a0, R &a1) {
-    const uint32_t cm = os.cm, cv = os.cv;
-    const R u0 = os.ui[0].x, u1 = os.ui[1].x, u2 = os.ui[2].x, u3 = os.ui[3].x;
-    R g[4] = {}, h[4] = {};
-    if (NA > 0) for (int e = 0; e < 4; ++e) g[e] = os.g0[e].x;
-    if (NA > 1) for (int e = 0; e < 4; ++e) h[e] = os.g1[e].x;
-#pragma unroll
-    for (int j = 0; j < NP; ++j) {
-        if (!ok[j] || (CHK && (i0[j] & cm) != cv)) continue;
-        if (NA > 0) {
-            const R xx = rdot<R>(lx[j], px[j]), xy = rdot<R>(lx[j], py[j]), yx = rdot<R>(ly[j], px[j]),
-                    yy = rdot<R>(ly[j], py[j]);
-            a0 += g[0] * xx + g[1] * xy + g[2] * yx + g[3] * yy;
-            if (NA > 1) a1 += h[0] * xx + h[1] * xy + h[2] * yx + h[3] * yy;
-        }
-        rmad_ip<R>(u0, u1, u2, u3, px[j], py[j]);
-        rmad_ip<R>(u0, u1, u2, u3, lx[j], ly[j]);
-    }
-}
-
-// one real antisymmetric generator [[0, -g], [g, 0]]:
-// Re<l|G|psi> = g (Re(conj(ly) x) - Re(conj(lx) y))
-template <typename R, int NP, bool CHK>
-__device__ __forceinline__ void run_pair_real_as(const AdjFOp<R> &os, const bool (&ok)[NP], const uint32_t (&i0)[NP],
-                                                 cplx<R> (&px)[NP], cplx<R> (&py)[NP], cplx<R> (&lx)[NP],
-                                                 cplx<R> (&ly)[NP], R &a0) {
-    const uint32_t cm = os.cm, cv = os.cv;
-    const R u0 = os.ui[0].x, u1 = os.ui[1].x, u2 = os.ui[2].x, u3 = os.ui[3].x;
-    R t = R(0);
-#pragma unroll
-    for (int j = 0; j < NP; ++j) {
-        if (!ok[j] || (CHK && (i0[j] & cm) != cv)) continue;
-        t = fma(ly[j].x, px[j].x, t);
-        t = fma(ly[j].y, px[j].y, t);
-        t = fma(-lx[j].x, py[j].x, t);
-        t = fma(-lx[j].y, py[j].y, t);
-        rmad_ip<R>(u0, u1, u2, u3, px[j], py[j]);
-        rmad_ip<R>(u0, u1, u2, u3, lx[j], ly[j]);
-    }
-    a0 += os.g0[2].x * t;
-}
+// A run acts on up to three tile bits, its roles 0, 1 and 2 (masks RA[r];
+// a run with fewer target bits takes other tile bits for the spare roles).
+// Each thread holds NO octets of psi and of lambda in registers: element e
+// of octet o is tile index q[o] | off[e], off[e] = the OR of RA[r] over the
+// set bits r of e.  A step on role RR pairs element e (bit RR clear) with
+// e | 2^RR, so which registers form a pair is known at compile time.  Octets
+// o >= nov hold no tile elements (the same count for every thread).
 
 template <typename R, int NA>
 __device__ __forceinline__ void diag_elem(cplx<R> d, cplx<R> g, cplx<R> h, cplx<R> &x, cplx<R> &l, R &a0, R &a1) {
@@ -457,14 +388,114 @@ __device__ __forceinline__ void diag_elem_im(cplx<R> d, R g, cplx<R> &x, cplx<R>
     cmul_ip<R>(d, l);
 }
 
-// DK: where the diagonal's bit lies.  0: the run's own bit (the pair's
-// elements take d0 and d1); 1: an outer bit (one entry for the whole tile);
-// 2: another tile bit (one entry per pair); 3: the run's other bit (the
-// first half of the pair arrays has it clear, the second half set).
-template <typename R, int NP, int NA, bool CHK, int DK, bool IM>
-__device__ __forceinline__ void run_diag(const AdjFOp<R> &os, bool outer_one, uint32_t tb, const bool (&ok)[NP],
-                                         const uint32_t (&i0)[NP], cplx<R> (&px)[NP], cplx<R> (&py)[NP],
-                                         cplx<R> (&lx)[NP], cplx<R> (&ly)[NP], R &a0, R &a1) {
+// exchange (C-NOT-like step) on role RR where the controls hold
+template <typename R, int NO, int RR, bool CHK>
+__device__ __forceinline__ void o_exchange(uint32_t cm, uint32_t cv, int nov, const uint32_t (&q)[NO],
+                                           const uint32_t (&off)[8], cplx<R> (&ps)[NO][8], cplx<R> (&ls)[NO][8]) {
+#pragma unroll
+    for (int o = 0; o < NO; ++o) {
+        if (o >= nov) continue;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            if ((e >> RR) & 1) continue;
+            const int e1 = e | (1 << RR);
+            const bool p = !CHK || ((q[o] | off[e]) & cm) == cv;
+            cswap_ip<R>(p, ps[o][e], ps[o][e1]);
+            cswap_ip<R>(p, ls[o][e], ls[o][e1]);
+        }
+    }
+}
+
+// complex U^dagger on role RR, NA generators accumulated
+template <typename R, int NO, int RR, int NA, bool CHK>
+__device__ __forceinline__ void o_pair(const AdjFOp<R> &os, int nov, const uint32_t (&q)[NO], const uint32_t (&off)[8],
+                                       cplx<R> (&ps)[NO][8], cplx<R> (&ls)[NO][8], R &a0, R &a1) {
+    const uint32_t cm = os.cm, cv = os.cv;
+    const cplx<R> u0 = os.ui[0], u1 = os.ui[1], u2 = os.ui[2], u3 = os.ui[3];
+    cplx<R> g[4], h[4];
+    if (NA > 0) for (int k = 0; k < 4; ++k) g[k] = os.g0[k];
+    if (NA > 1) for (int k = 0; k < 4; ++k) h[k] = os.g1[k];
+#pragma unroll
+    for (int o = 0; o < NO; ++o) {
+        if (o >= nov) continue;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            if ((e >> RR) & 1) continue;
+            const int e1 = e | (1 << RR);
+            if (CHK && ((q[o] | off[e]) & cm) != cv) continue;
+            if (NA > 0) a0 += pair_grad<R>(g, ps[o][e], ps[o][e1], ls[o][e], ls[o][e1]);
+            if (NA > 1) a1 += pair_grad<R>(h, ps[o][e], ps[o][e1], ls[o][e], ls[o][e1]);
+            cmad_ip<R>(u0, u1, u2, u3, ps[o][e], ps[o][e1]);
+            cmad_ip<R>(u0, u1, u2, u3, ls[o][e], ls[o][e1]);
+        }
+    }
+}
+
+// real U^dagger and real generators: Re<l|g x> = g Re(conj(l) x) term by term
+template <typename R, int NO, int RR, int NA, bool CHK>
+__device__ __forceinline__ void o_pair_real(const AdjFOp<R> &os, int nov, const uint32_t (&q)[NO],
+                                            const uint32_t (&off)[8], cplx<R> (&ps)[NO][8], cplx<R> (&ls)[NO][8],
+                                            R &a0, R &a1) {
+    const uint32_t cm = os.cm, cv = os.cv;
+    const R u0 = os.ui[0].x, u1 = os.ui[1].x, u2 = os.ui[2].x, u3 = os.ui[3].x;
+    R g[4] = {}, h[4] = {};
+    if (NA > 0) for (int k = 0; k < 4; ++k) g[k] = os.g0[k].x;
+    if (NA > 1) for (int k = 0; k < 4; ++k) h[k] = os.g1[k].x;
+#pragma unroll
+    for (int o = 0; o < NO; ++o) {
+        if (o >= nov) continue;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            if ((e >> RR) & 1) continue;
+            const int e1 = e | (1 << RR);
+            if (CHK && ((q[o] | off[e]) & cm) != cv) continue;
+            if (NA > 0) {
+                const R xx = rdot<R>(ls[o][e], ps[o][e]), xy = rdot<R>(ls[o][e], ps[o][e1]),
+                        yx = rdot<R>(ls[o][e1], ps[o][e]), yy = rdot<R>(ls[o][e1], ps[o][e1]);
+                a0 += g[0] * xx + g[1] * xy + g[2] * yx + g[3] * yy;
+                if (NA > 1) a1 += h[0] * xx + h[1] * xy + h[2] * yx + h[3] * yy;
+            }
+            rmad_ip<R>(u0, u1, u2, u3, ps[o][e], ps[o][e1]);
+            rmad_ip<R>(u0, u1, u2, u3, ls[o][e], ls[o][e1]);
+        }
+    }
+}
+
+// one real antisymmetric generator [[0, -g], [g, 0]]:
+// Re<l|G|psi> = g (Re(conj(ly) x) - Re(conj(lx) y))
+template <typename R, int NO, int RR, bool CHK>
+__device__ __forceinline__ void o_pair_ras(const AdjFOp<R> &os, int nov, const uint32_t (&q)[NO],
+                                           const uint32_t (&off)[8], cplx<R> (&ps)[NO][8], cplx<R> (&ls)[NO][8],
+                                           R &a0) {
+    const uint32_t cm = os.cm, cv = os.cv;
+    const R u0 = os.ui[0].x, u1 = os.ui[1].x, u2 = os.ui[2].x, u3 = os.ui[3].x;
+    R t = R(0);
+#pragma unroll
+    for (int o = 0; o < NO; ++o) {
+        if (o >= nov) continue;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            if ((e >> RR) & 1) continue;
+            const int e1 = e | (1 << RR);
+            if (CHK && ((q[o] | off[e]) & cm) != cv) continue;
+            t = fma(ls[o][e1].x, ps[o][e].x, t);
+            t = fma(ls[o][e1].y, ps[o][e].y, t);
+            t = fma(-ls[o][e].x, ps[o][e1].x, t);
+            t = fma(-ls[o][e].y, ps[o][e1].y, t);
+            rmad_ip<R>(u0, u1, u2, u3, ps[o][e], ps[o][e1]);
+            rmad_ip<R>(u0, u1, u2, u3, ls[o][e], ls[o][e1]);
+        }
+    }
+    a0 += os.g0[2].x * t;
+}
+
+// Diagonal step.  DK 0: its bit is role RR (element e takes entry 0 or 1 by
+// bit RR of e); DK 1: an outer bit (one entry for the tile, chosen by the
+// caller into d0); DK 2: another tile bit (one entry per octet).
+template <typename R, int NO, int RR, int NA, bool CHK, int DK, bool IM>
+__device__ __forceinline__ void o_diag(const AdjFOp<R> &os, bool outer_one, int nov, const uint32_t (&q)[NO],
+                                       const uint32_t (&off)[8], cplx<R> (&ps)[NO][8], cplx<R> (&ls)[NO][8], R &a0,
+                                       R &a1) {
     const uint32_t cm = os.cm, cv = os.cv;
     const int tpos = os.tpos;
     cplx<R> d0 = os.ui[0], d1 = os.ui[3];
@@ -473,65 +504,94 @@ __device__ __forceinline__ void run_diag(const AdjFOp<R> &os, bool outer_one, ui
     if (NA > 1) { h0 = os.g1[0]; h3 = os.g1[3]; }
     if (DK == 1 && outer_one) { d0 = d1; g0 = g3; h0 = h3; }
 #pragma unroll
-    for (int j = 0; j < NP; ++j) {
-        if (!ok[j]) continue;
-        const uint32_t e0 = i0[j], e1 = i0[j] | tb;
-        cplx<R> da = d0, db = d1, ga = g0, gb = g3, ha = h0, hb = h3;
-        if (DK == 1) { db = d0; gb = g0; hb = h0; }
-        if (DK == 2 || DK == 3) {
-            const bool one = DK == 3 ? j >= NP / 2 : ((e0 >> tpos) & 1) != 0;
-            da = db = one ? d1 : d0;
-            if (NA > 0) ga = gb = one ? g3 : g0;
-            if (NA > 1) ha = hb = one ? h3 : h0;
-        }
-        if (IM) {
-            if (!CHK || (e0 & cm) == cv) diag_elem_im<R>(da, ga.y, px[j], lx[j], a0);
-            if (!CHK || (e1 & cm) == cv) diag_elem_im<R>(db, gb.y, py[j], ly[j], a0);
-        } else {
-            if (!CHK || (e0 & cm) == cv) diag_elem<R, NA>(da, ga, ha, px[j], lx[j], a0, a1);
-            if (!CHK || (e1 & cm) == cv) diag_elem<R, NA>(db, gb, hb, py[j], ly[j], a0, a1);
+    for (int o = 0; o < NO; ++o) {
+        if (o >= nov) continue;
+        bool oone = false;
+        if (DK == 2) oone = (q[o] >> tpos) & 1;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            bool one = false;
+            if (DK == 0) one = (e >> RR) & 1;
+            if (DK == 2) one = oone;
+            const cplx<R> d = one ? d1 : d0;
+            const cplx<R> g = one ? g3 : g0, h = one ? h3 : h0;
+            if (CHK && ((q[o] | off[e]) & cm) != cv) continue;
+            if (IM) diag_elem_im<R>(d, g.y, ps[o][e], ls[o][e], a0);
+            else diag_elem<R, NA>(d, g, h, ps[o][e], ls[o][e], a0, a1);
         }
     }
 }
 
-template <typename R, int NP, int NA, bool CHK, bool IM>
-__device__ __forceinline__ void run_diag_any(const AdjFOp<R> &os, uint64_t base, uint32_t tb, uint32_t ob,
-                                             const bool (&ok)[NP], const uint32_t (&i0)[NP], cplx<R> (&px)[NP],
-                                             cplx<R> (&py)[NP], cplx<R> (&lx)[NP], cplx<R> (&ly)[NP], R &a0, R &a1) {
-    if (os.mode == 3) {
-        const bool outer_one = (base >> os.tpos) & 1;
-        run_diag<R, NP, NA, CHK, 1, IM>(os, outer_one, tb, ok, i0, px, py, lx, ly, a0, a1);
-    } else if ((1u << os.tpos) == tb) {
-        run_diag<R, NP, NA, CHK, 0, IM>(os, false, tb, ok, i0, px, py, lx, ly, a0, a1);
-    } else if ((1u << os.tpos) == ob) {
-        run_diag<R, NP, NA, CHK, 3, IM>(os, false, tb, ok, i0, px, py, lx, ly, a0, a1);
-    } else {
-        run_diag<R, NP, NA, CHK, 2, IM>(os, false, tb, ok, i0, px, py, lx, ly, a0, a1);
-    }
-}
-
-template <typename R, int NP, bool CHK>
-__device__ __forceinline__ void step_on_pairs(const AdjFOp<R> &os, uint64_t base, uint32_t tb, uint32_t ob,
-                                              const bool (&ok)[NP],
-                                              const uint32_t (&i0)[NP], cplx<R> (&px)[NP], cplx<R> (&py)[NP],
-                                              cplx<R> (&lx)[NP], cplx<R> (&ly)[NP], R &a0, R &a1) {
+// The step kinds of role RR (pair steps and diagonals on role RR's bit).
+template <typename R, int NO, int RR, bool CHK>
+__device__ __forceinline__ void step_role(const AdjFOp<R> &os, int nov, const uint32_t (&q)[NO],
+                                          const uint32_t (&off)[8], cplx<R> (&ps)[NO][8], cplx<R> (&ls)[NO][8],
+                                          R &a0, R &a1) {
     const int mode = os.mode, nang = os.nang;
     if (mode == 1) {
-        run_exchange<R, NP, CHK>(os.cm, os.cv, ok, i0, px, py, lx, ly);
+        o_exchange<R, NO, RR, CHK>(os.cm, os.cv, nov, q, off, ps, ls);
     } else if (mode == 4) {
-        if (os.gk == 1) run_pair_real_as<R, NP, CHK>(os, ok, i0, px, py, lx, ly, a0);
-        else if (nang == 0) run_pair_real<R, NP, 0, CHK>(os, ok, i0, px, py, lx, ly, a0, a1);
-        else if (nang == 1) run_pair_real<R, NP, 1, CHK>(os, ok, i0, px, py, lx, ly, a0, a1);
-        else run_pair_real<R, NP, 2, CHK>(os, ok, i0, px, py, lx, ly, a0, a1);
+        if (os.gk == 1) o_pair_ras<R, NO, RR, CHK>(os, nov, q, off, ps, ls, a0);
+        else if (nang == 0) o_pair_real<R, NO, RR, 0, CHK>(os, nov, q, off, ps, ls, a0, a1);
+        else if (nang == 1) o_pair_real<R, NO, RR, 1, CHK>(os, nov, q, off, ps, ls, a0, a1);
+        else o_pair_real<R, NO, RR, 2, CHK>(os, nov, q, off, ps, ls, a0, a1);
     } else if (mode == 0) {
-        if (nang == 0) run_pair<R, NP, 0, CHK>(os, ok, i0, px, py, lx, ly, a0, a1);
-        else if (nang == 1) run_pair<R, NP, 1, CHK>(os, ok, i0, px, py, lx, ly, a0, a1);
-        else run_pair<R, NP, 2, CHK>(os, ok, i0, px, py, lx, ly, a0, a1);
-    } else {
-        if (os.gk == 2) run_diag_any<R, NP, 1, CHK, true>(os, base, tb, ob, ok, i0, px, py, lx, ly, a0, a1);
-        else if (nang == 0) run_diag_any<R, NP, 0, CHK, false>(os, base, tb, ob, ok, i0, px, py, lx, ly, a0, a1);
-        else if (nang == 1) run_diag_any<R, NP, 1, CHK, false>(os, base, tb, ob, ok, i0, px, py, lx, ly, a0, a1);
-        else run_diag_any<R, NP, 2, CHK, false>(os, base, tb, ob, ok, i0, px, py, lx, ly, a0, a1);
+        if (nang == 0) o_pair<R, NO, RR, 0, CHK>(os, nov, q, off, ps, ls, a0, a1);
+        else if (nang == 1) o_pair<R, NO, RR, 1, CHK>(os, nov, q, off, ps, ls, a0, a1);
+        else o_pair<R, NO, RR, 2, CHK>(os, nov, q, off, ps, ls, a0, a1);
+    } else {   // diagonal on this role's bit
+        if (os.gk == 2) o_diag<R, NO, RR, 1, CHK, 0, true>(os, false, nov, q, off, ps, ls, a0, a1);
+        else if (nang == 0) o_diag<R, NO, RR, 0, CHK, 0, false>(os, false, nov, q, off, ps, ls, a0, a1);
+        else if (nang == 1) o_diag<R, NO, RR, 1, CHK, 0, false>(os, false, nov, q, off, ps, ls, a0, a1);
+        else o_diag<R, NO, RR, 2, CHK, 0, false>(os, false, nov, q, off, ps, ls, a0, a1);
+    }
+}
+
+// A diagonal step whose bit is not one of the run's roles: an outer bit
+// (mode 3) or another tile bit (mode 2).
+template <typename R, int NO, bool CHK, int DK>
+__device__ __forceinline__ void step_diag_other(const AdjFOp<R> &os, bool outer_one, int nov, const uint32_t (&q)[NO],
+                                                const uint32_t (&off)[8], cplx<R> (&ps)[NO][8], cplx<R> (&ls)[NO][8],
+                                                R &a0, R &a1) {
+    const int nang = os.nang;
+    if (os.gk == 2) o_diag<R, NO, 0, 1, CHK, DK, true>(os, outer_one, nov, q, off, ps, ls, a0, a1);
+    else if (nang == 0) o_diag<R, NO, 0, 0, CHK, DK, false>(os, outer_one, nov, q, off, ps, ls, a0, a1);
+    else if (nang == 1) o_diag<R, NO, 0, 1, CHK, DK, false>(os, outer_one, nov, q, off, ps, ls, a0, a1);
+    else o_diag<R, NO, 0, 2, CHK, DK, false>(os, outer_one, nov, q, off, ps, ls, a0, a1);
+}
+
+template <typename R, int NO, bool CHK>
+__device__ __forceinline__ void step_octets(const AdjFOp<R> &os, uint64_t base, int nov, const uint32_t (&q)[NO],
+                                            const uint32_t (&off)[8], cplx<R> (&ps)[NO][8], cplx<R> (&ls)[NO][8],
+                                            R &a0, R &a1) {
+    const int role = os.role;
+    if (role == 0) step_role<R, NO, 0, CHK>(os, nov, q, off, ps, ls, a0, a1);
+    else if (role == 1) step_role<R, NO, 1, CHK>(os, nov, q, off, ps, ls, a0, a1);
+    else if (role == 2) step_role<R, NO, 2, CHK>(os, nov, q, off, ps, ls, a0, a1);
+    else if (os.mode == 3) step_diag_other<R, NO, CHK, 1>(os, (base >> os.tpos) & 1, nov, q, off, ps, ls, a0, a1);
+    else step_diag_other<R, NO, CHK, 2>(os, false, nov, q, off, ps, ls, a0, a1);
+}
+
+// The run's leading exchange steps as a permutation of each octet's
+// places: field e (3 bits) of perm names the element whose value place e
+// takes at the load.  An exchange on role RR swaps fields e and e | 2^RR
+// where its controls hold on the place's index.
+template <int NO, int RR>
+__device__ __forceinline__ void o_pre(uint32_t cm, uint32_t cv, int nov, const uint32_t (&q)[NO],
+                                      const uint32_t (&off)[8], uint32_t (&perm)[NO]) {
+#pragma unroll
+    for (int o = 0; o < NO; ++o) {
+        if (o >= nov) continue;
+        uint32_t x = perm[o];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            if ((e >> RR) & 1) continue;
+            const int e1 = e | (1 << RR);
+            const bool c = ((q[o] | off[e]) & cm) == cv;
+            const uint32_t d = ((x >> (3 * e)) ^ (x >> (3 * e1))) & (c ? 7u : 0u);
+            x ^= (d << (3 * e)) | (d << (3 * e1));
+        }
+        perm[o] = x;
     }
 }
 
@@ -588,6 +648,9 @@ template <typename R>
 constexpr int adj_full_k() { return sizeof(R) == 4 ? 12 : 11; }
 template <typename R>
 constexpr int adj_np() { return (1 << (adj_full_k<R>() - 1)) / AF_THREADS; }
+// the fused sweep needs a tile of at least one octet per thread
+template <typename R>
+constexpr bool adj_fused_ok(int n) { return (1 << (n < adj_full_k<R>() ? n : adj_full_k<R>())) >= 8 * AF_THREADS; }
 
 template <typename R>
 __global__ void __launch_bounds__(AF_THREADS, QS_AF_MINB) k_adj_pass(cplx<R> *__restrict__ psi, cplx<R> *__restrict__ lam,
@@ -597,11 +660,13 @@ __global__ void __launch_bounds__(AF_THREADS, QS_AF_MINB) k_adj_pass(cplx<R> *__
     extern __shared__ __align__(16) unsigned char smraw[];
     const int K = P.K;
     const uint32_t T = 1u << K;
-    // quadruples per thread that hold tile elements: the tile has T / 4
-    // quadruples, a whole number of CTA-wide rows of them (K >= the tile bits
-    // of one row, which the host guarantees), so the count is the same for
-    // every thread and the tests on it do not diverge
-    const int nqv = int(T / 4 / AF_THREADS);
+    // octets per thread that hold tile elements: the tile has T / 8 octets, a
+    // whole number of CTA-wide rows of them (the host guarantees at least
+    // one), so the count is the same for every thread and the tests on it do
+    // not diverge (a compile-time count, all octets full, let the compiler
+    // schedule the run bodies into 4 KB of spills)
+    constexpr int NO = NP / 4;
+    const int nov = int(T / 8 / AF_THREADS);
     cplx<R> *sp = reinterpret_cast<cplx<R> *>(smraw);
     cplx<R> *sl = sp + T;
     Acc<R> *sacc = reinterpret_cast<Acc<R> *>(sl + T);                        // nacc x AF_WARPS
@@ -634,119 +699,74 @@ __global__ void __launch_bounds__(AF_THREADS, QS_AF_MINB) k_adj_pass(cplx<R> *__
         __syncthreads();
         int k0 = 0;
         for (int r = 0; r < P.nrun; ++r) {
-            // A run acts on one or two tile bits, A = 2^t and B: each thread
-            // keeps NQ quadruples (i, i|A, i|B, i|A|B) of psi and lambda in
-            // registers (a one-bit run takes any other tile bit as B).  The
-            // pair arrays hold the quadruples as the pairs of the bit the
-            // current step needs: on A, (i, i|A) and (i|B, i|A|B); on B,
-            // (i, i|B) and (i|A, i|A|B); switching bits exchanges the middle
-            // elements (register moves).  Diagonal steps take either.
-            constexpr int NQ = NP / 2;
-            const int t = P.run_bit[r], len = P.run_len[r];
-            const int t2 = P.run_bit2[r] != 0xff ? P.run_bit2[r] : (t == 0 ? 1 : 0);
-            const uint32_t A = 1u << t, B = 1u << t2;
-            const int lo = t < t2 ? t : t2, hi = t < t2 ? t2 : t;
-            uint32_t i0[NP];
-            bool ok[NP];
-            cplx<R> px[NP], py[NP], lx[NP], ly[NP];
+            const int len = P.run_len[r];
+            const uint32_t RA0 = 1u << P.run_bit[r], RA1 = 1u << P.run_bit2[r], RA2 = 1u << P.run_bit3[r];
+            // the three role bits ascending, for the octet index
+            int s0 = P.run_bit[r], s1 = P.run_bit2[r], s2 = P.run_bit3[r];
+            if (s0 > s1) { const int t = s0; s0 = s1; s1 = t; }
+            if (s1 > s2) { const int t = s1; s1 = s2; s2 = t; }
+            if (s0 > s1) { const int t = s0; s0 = s1; s1 = t; }
+            uint32_t off[8];
 #pragma unroll
-            for (int j = 0; j < NQ; ++j) {
-                const uint32_t p = tid + uint32_t(j) * AF_THREADS;
-                const uint32_t x = ((p >> lo) << (lo + 1)) | (p & ((1u << lo) - 1u));
-                const uint32_t q = ((x >> hi) << (hi + 1)) | (x & ((1u << hi) - 1u));
-                ok[j] = ok[NQ + j] = j < nqv;
-                i0[j] = q;
-                i0[NQ + j] = q | B;
+            for (int e = 0; e < 8; ++e) off[e] = ((e & 1) ? RA0 : 0u) | ((e & 2) ? RA1 : 0u) | ((e & 4) ? RA2 : 0u);
+            uint32_t q[NO];
+#pragma unroll
+            for (int o = 0; o < NO; ++o) {
+                uint32_t x = tid + uint32_t(o) * AF_THREADS;
+                x = ((x >> s0) << (s0 + 1)) | (x & ((1u << s0) - 1u));
+                x = ((x >> s1) << (s1 + 1)) | (x & ((1u << s1) - 1u));
+                x = ((x >> s2) << (s2 + 1)) | (x & ((1u << s2) - 1u));
+                q[o] = x;
             }
-            // the run's leading exchange steps (C-NOT-like, on bit A or B)
-            // become the choice of which element of each quadruple loads into
-            // which place: perm holds, in 2-bit fields, the source element
-            // (a + 2b for the offset a A + b B) of each place
-            uint32_t perm[NQ];
-#pragma unroll
-            for (int j = 0; j < NQ; ++j) perm[j] = 0xE4u;   // place e <- element e
+            cplx<R> ps[NO][8], ls[NO][8];
             const int pre = P.run_pre[r];
+            // the run's leading exchange steps become the choice of which
+            // element loads into which place (none: place e <- element e)
+            uint32_t perm[NO];
+#pragma unroll
+            for (int o = 0; o < NO; ++o) perm[o] = 0xFAC688u;
             for (int k = k0; k < k0 + pre; ++k) {
                 const AdjFOp<R> &os = sops[k];
                 if ((base & os.om) != os.ov) continue;
-                const uint32_t cm = os.cm, cv = os.cv;
-                const bool sb = os.tpos == t2;                // exchange on B, else on A
-                const int e1 = sb ? 2 : 1, f0 = sb ? 1 : 2;   // pairs (0, e1) and (f0, 3)
-#pragma unroll
-                for (int j = 0; j < NQ; ++j) {
-                    const uint32_t q = i0[j];
-                    const bool c0 = (q & cm) == cv, c1 = ((sb ? q | A : q | B) & cm) == cv;
-                    uint32_t x = perm[j];
-                    uint32_t d = (x ^ (x >> (2 * e1))) & (c0 ? 3u : 0u);
-                    x ^= d | (d << (2 * e1));
-                    d = ((x >> (2 * f0)) ^ (x >> 6)) & (c1 ? 3u : 0u);
-                    x ^= (d << (2 * f0)) | (d << 6);
-                    perm[j] = x;
-                }
+                if (os.role == 0) o_pre<NO, 0>(os.cm, os.cv, nov, q, off, perm);
+                else if (os.role == 1) o_pre<NO, 1>(os.cm, os.cv, nov, q, off, perm);
+                else o_pre<NO, 2>(os.cm, os.cv, nov, q, off, perm);
             }
 #pragma unroll
-            for (int j = 0; j < NQ; ++j) {
-                if (ok[j]) {
-                    const uint32_t q = i0[j], x = perm[j];
-                    uint32_t off[4];
+            for (int o = 0; o < NO; ++o) {
+                if (o >= nov) continue;
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const uint32_t src = (x >> (2 * e)) & 3u;
-                        off[e] = ((src & 1u) ? A : 0u) | ((src & 2u) ? B : 0u);
-                    }
-                    px[j] = sp[q | off[0]]; py[j] = sp[q | off[1]];
-                    px[NQ + j] = sp[q | off[2]]; py[NQ + j] = sp[q | off[3]];
-                    lx[j] = sl[q | off[0]]; ly[j] = sl[q | off[1]];
-                    lx[NQ + j] = sl[q | off[2]]; ly[NQ + j] = sl[q | off[3]];
+                for (int e = 0; e < 8; ++e) {
+                    const uint32_t src = (perm[o] >> (3 * e)) & 7u;
+                    const uint32_t idx = q[o] | ((src & 1u) ? RA0 : 0u) | ((src & 2u) ? RA1 : 0u) |
+                                         ((src & 4u) ? RA2 : 0u);
+                    ps[o][e] = sp[idx];
+                    ls[o][e] = sl[idx];
                 }
             }
-            bool onB = false;   // the arrays hold the pairs of bit B
             for (int k = k0 + pre; k < k0 + len; ++k) {
                 const AdjFOp<R> &os = sops[k];
                 if ((base & os.om) != os.ov) continue;            // the same for the whole tile
-                const bool diagonal = os.mode == 2 || os.mode == 3;
-                const bool wantB = !diagonal && os.tpos == t2;
-                if (!diagonal && wantB != onB) {
-#pragma unroll
-                    for (int j = 0; j < NQ; ++j) {
-                        const cplx<R> a = py[j];
-                        py[j] = px[NQ + j]; px[NQ + j] = a;
-                        const cplx<R> c = ly[j];
-                        ly[j] = lx[NQ + j]; lx[NQ + j] = c;
-                        i0[NQ + j] = i0[j] | (wantB ? A : B);
-                    }
-                    onB = wantB;
-                }
-                const uint32_t tbv = onB ? B : A, obv = onB ? A : B;
                 const int nang = os.nang;
                 R a0 = R(0), a1 = R(0);
-                if (os.cm == 0) step_on_pairs<R, NP, false>(os, base, tbv, obv, ok, i0, px, py, lx, ly, a0, a1);
-                else step_on_pairs<R, NP, true>(os, base, tbv, obv, ok, i0, px, py, lx, ly, a0, a1);
+                if (os.cm == 0) step_octets<R, NO, false>(os, base, nov, q, off, ps, ls, a0, a1);
+                else step_octets<R, NO, true>(os, base, nov, q, off, ps, ls, a0, a1);
                 if (nang > 0) {
-                    const R s0 = warp_sum<R>(a0);
-                    if (lane == 0) acc_add<R>(sacc[os.acc * AF_WARPS + warp], s0);
+                    const R s0v = warp_sum<R>(a0);
+                    if (lane == 0) acc_add<R>(sacc[os.acc * AF_WARPS + warp], s0v);
                     if (nang > 1) {
-                        const R s1 = warp_sum<R>(a1);
-                        if (lane == 0) acc_add<R>(sacc[(os.acc + 1) * AF_WARPS + warp], s1);
+                        const R s1v = warp_sum<R>(a1);
+                        if (lane == 0) acc_add<R>(sacc[(os.acc + 1) * AF_WARPS + warp], s1v);
                     }
                 }
             }
-            // back to the pairs of bit A, then to shared memory
-            if (onB) {
 #pragma unroll
-                for (int j = 0; j < NQ; ++j) {
-                    const cplx<R> a = py[j];
-                    py[j] = px[NQ + j]; px[NQ + j] = a;
-                    const cplx<R> c = ly[j];
-                    ly[j] = lx[NQ + j]; lx[NQ + j] = c;
-                    i0[NQ + j] = i0[j] | B;
-                }
-            }
+            for (int o = 0; o < NO; ++o) {
+                if (o >= nov) continue;
 #pragma unroll
-            for (int j = 0; j < NP; ++j) {
-                if (ok[j]) {
-                    sp[i0[j]] = px[j]; sp[i0[j] | A] = py[j];
-                    sl[i0[j]] = lx[j]; sl[i0[j] | A] = ly[j];
+                for (int e = 0; e < 8; ++e) {
+                    sp[q[o] | off[e]] = ps[o][e];
+                    sl[q[o] | off[e]] = ls[o][e];
                 }
             }
             k0 += len;
@@ -791,15 +811,17 @@ bool real_gens(const AdjStep &d) {
 // Orders a pass's steps (idx, in sweep order) into runs: the next step is the
 // first ready one (every earlier step it does not commute with already
 // placed) that is diagonal or targets one of the current run's bits (a run
-// takes up to two target bits; a second bit joins with the first step on it);
+// takes up to three target bits; a new bit joins with the first step on it);
 // when none is, the run ends and the first ready step opens the next.  Two
 // steps commute when every index bit they share is a control or the target
 // of a diagonal step for both (the test the pass planner uses), and moving a
 // step past steps it commutes with leaves every gradient term unchanged.
+constexpr int RUN_BITS = 3;
 struct Run {
     int len;    // steps
-    int bit;    // global target bit, -1 for a run of diagonal steps only
-    int bit2;   // second global target bit, -1 for none
+    int bit;    // global target bits, -1 for none (bit = -1: diagonal steps only)
+    int bit2;
+    int bit3;
 };
 
 void schedule_runs(const std::vector<int> &idx, const std::vector<AdjStep> &steps, const std::vector<HostOp> &hops,
@@ -823,12 +845,11 @@ void schedule_runs(const std::vector<int> &idx, const std::vector<AdjStep> &step
         if (npred[k] == 0) ready.insert(int(k));
     order.clear();
     runs.clear();
-    int cur = -1, cur2 = -1, len = 0;
+    int cur[RUN_BITS] = {-1, -1, -1}, len = 0;
     bool lead = true;   // the run holds exchange steps only so far
-    auto fits = [&](int k) {
-        const int b = hops[size_t(idx[size_t(k)])].bit;
-        return b == cur || b == cur2 || cur < 0 || cur2 < 0;
-    };
+    auto has = [&](int b) { return b == cur[0] || b == cur[1] || b == cur[2]; };
+    auto free_slot = [&]() { return cur[RUN_BITS - 1] < 0; };
+    auto fits = [&](int k) { return has(hops[size_t(idx[size_t(k)])].bit) || free_slot(); };
     while (order.size() < m) {
         int pick = -1;
         // while the run is only exchanges: another exchange on one of its
@@ -840,14 +861,13 @@ void schedule_runs(const std::vector<int> &idx, const std::vector<AdjStep> &step
         if (pick < 0)
             for (int k : ready) {
                 const int b = hops[size_t(idx[size_t(k)])].bit;
-                if (diag[size_t(k)] || b == cur || b == cur2) { pick = k; break; }
+                if (diag[size_t(k)] || has(b)) { pick = k; break; }
             }
-        if (pick < 0)
-            for (int k : ready)
-                if (cur < 0 || cur2 < 0) { pick = k; break; }
+        if (pick < 0 && free_slot())
+            for (int k : ready) { pick = k; break; }
         if (pick < 0) {
-            runs.push_back({len, cur, cur2});
-            cur = cur2 = -1;
+            runs.push_back({len, cur[0], cur[1], cur[2]});
+            cur[0] = cur[1] = cur[2] = -1;
             len = 0;
             lead = true;
             continue;
@@ -855,8 +875,9 @@ void schedule_runs(const std::vector<int> &idx, const std::vector<AdjStep> &step
         if (steps[size_t(idx[size_t(pick)])].cls != AC_X) lead = false;
         if (!diag[size_t(pick)]) {
             const int b = hops[size_t(idx[size_t(pick)])].bit;
-            if (cur < 0) cur = b;
-            else if (b != cur && cur2 < 0) cur2 = b;
+            if (!has(b))
+                for (int r = 0; r < RUN_BITS; ++r)
+                    if (cur[r] < 0) { cur[r] = b; break; }
         }
         order.push_back(idx[size_t(pick)]);
         ++len;
@@ -864,7 +885,7 @@ void schedule_runs(const std::vector<int> &idx, const std::vector<AdjStep> &step
         for (int sidx : succ[size_t(pick)])
             if (--npred[size_t(sidx)] == 0) ready.insert(sidx);
     }
-    if (len > 0) runs.push_back({len, cur, cur2});
+    if (len > 0) runs.push_back({len, cur[0], cur[1], cur[2]});
 }
 
 // One tile pass of the fused reverse sweep, planned on the host: the tile's
@@ -907,9 +928,9 @@ bool plan_sweep(int n, int K, const std::vector<AdjStep> &steps, const std::vect
         for (size_t r = 0, k = 0; r < sp.runs.size(); k += size_t(sp.runs[r].len), ++r) {
             // leading exchanges on the run's bits fold into the load
             int pre = 0;
+            auto on_run = [&](int b) { return b == sp.runs[r].bit || b == sp.runs[r].bit2 || b == sp.runs[r].bit3; };
             while (pre < sp.runs[r].len && steps[size_t(sp.order[k + size_t(pre)])].cls == AC_X &&
-                   (hops[size_t(sp.order[k + size_t(pre)])].bit == sp.runs[r].bit ||
-                    hops[size_t(sp.order[k + size_t(pre)])].bit == sp.runs[r].bit2))
+                   on_run(hops[size_t(sp.order[k + size_t(pre)])].bit))
                 ++pre;
             sp.pre.push_back(pre);
         }
@@ -941,14 +962,35 @@ cudaError_t fused_sweep(qs_state *s, const std::vector<AdjStep> &steps, const st
         offs.push_back(flat.size());
         if (sp.runs.size() > size_t(ADJ_MAX_OPS)) return cudaErrorInvalidValue;
         P.nrun = int(sp.runs.size());
+        // each run's three role bits (tile-local): its target bits, then the
+        // highest tile bits it does not target for the spare roles
+        std::vector<std::array<int, RUN_BITS>> roles(sp.runs.size());
+        std::vector<int> run_of;   // run of each op, in execution order
         for (size_t r = 0; r < sp.runs.size(); ++r) {
+            const int tb[RUN_BITS] = {sp.runs[r].bit, sp.runs[r].bit2, sp.runs[r].bit3};
+            std::array<int, RUN_BITS> &rl = roles[r];
+            uint32_t used = 0;
+            for (int i = 0; i < RUN_BITS; ++i) {
+                rl[size_t(i)] = tb[i] >= 0 ? local[tb[i]] : -1;
+                if (rl[size_t(i)] >= 0) used |= 1u << rl[size_t(i)];
+            }
+            for (int i = 0, b = K - 1; i < RUN_BITS; ++i) {
+                if (rl[size_t(i)] >= 0) continue;
+                while (b >= 0 && ((used >> b) & 1)) --b;
+                if (b < 0) return cudaErrorInvalidValue;
+                rl[size_t(i)] = b;
+                used |= 1u << b;
+            }
             P.run_len[r] = uint8_t(sp.runs[r].len);
-            P.run_bit[r] = uint8_t(sp.runs[r].bit < 0 ? K - 1 : local[sp.runs[r].bit]);
-            P.run_bit2[r] = uint8_t(sp.runs[r].bit2 < 0 ? 0xff : local[sp.runs[r].bit2]);
+            P.run_bit[r] = uint8_t(rl[0]);
+            P.run_bit2[r] = uint8_t(rl[1]);
+            P.run_bit3[r] = uint8_t(rl[2]);
             P.run_pre[r] = uint8_t(sp.pre[r]);
+            for (int i = 0; i < sp.runs[r].len; ++i) run_of.push_back(int(r));
         }
         int nacc = 0;
-        for (int j : sp.order) {
+        for (size_t oi = 0; oi < sp.order.size(); ++oi) {
+            const int j = sp.order[oi];
             const AdjStep &d = steps[size_t(j)];
             const HostOp &o = hops[size_t(j)];
             AdjFOp<R> f;
@@ -967,6 +1009,12 @@ cudaError_t fused_sweep(qs_state *s, const std::vector<AdjStep> &steps, const st
                 if (local[c] >= 0) { f.cm |= 1u << local[c]; if (one) f.cv |= 1u << local[c]; }
                 else { f.om |= uint64_t(1) << c; if (one) f.ov |= uint64_t(1) << c; }
             }
+            // the target bit's role in the op's run; 3 for a diagonal on no role bit
+            f.role = 3;
+            if (f.mode != 3)
+                for (int i = 0; i < RUN_BITS; ++i)
+                    if (roles[size_t(run_of[oi])][size_t(i)] == f.tpos) f.role = i;
+            if (f.role == 3 && f.mode != 2 && f.mode != 3) return cudaErrorInvalidValue;   // a pair step off its run
             f.nang = d.nang;
             // generator entries (re, im) at 2e, 2e + 1 for e = 0..3
             if (f.mode == 4 && d.nang == 1 && d.g0[0] == 0.0 && d.g0[6] == 0.0 && d.g0[2] == -d.g0[4]) f.gk = 1;
@@ -1124,7 +1172,7 @@ qs_status run_adjoint(qs_state *s, const std::vector<qs_gate> &gg, size_t n_para
     // fused sweep: tiles of 2^K amplitudes (64 KiB per vector), one CTA per
     // tile at a time, as many CTAs as fit
     const int Kf = std::min(n, adj_full_k<R>());
-    const bool fused = fuse && (size_t(1) << Kf) >= size_t(4) * AF_THREADS;   // a tile of at least one row of quadruples per thread
+    const bool fused = fuse && adj_fused_ok<R>(n);
     int nblk = RED_BLOCKS;
     if (fused) {
         // the largest pass: ADJ_MAX_OPS steps with two generators each
@@ -1255,7 +1303,7 @@ extern "C" qs_status qs_adjoint_describe(int n, qs_dtype dt, const qs_gate *g, s
                       o.u[3], o.u[4], o.u[5], o.u[6], o.u[7]);
         out += line;
     }
-    if (n >= 6) {
+    if (dt == QS_C64 ? adj_fused_ok<float>(n) : adj_fused_ok<double>(n)) {
         const int K = std::min(n, dt == QS_C64 ? adj_full_k<float>() : adj_full_k<double>());
         std::vector<SweepPass> plan;
         if (!plan_sweep(n, K, steps, hops, plan)) return fail(QS_EUNSUPPORTED, "adjoint plan: a target outside its tile");
@@ -1266,7 +1314,8 @@ extern "C" qs_status qs_adjoint_describe(int n, qs_dtype dt, const qs_gate *g, s
             size_t k = 0;
             for (size_t r = 0; r < plan[p].runs.size(); ++r) {
                 out += "run bit=" + std::to_string(plan[p].runs[r].bit) + " bit2=" + std::to_string(plan[p].runs[r].bit2) +
-                       " pre=" + std::to_string(plan[p].pre[r]) + " steps=";
+                       " bit3=" + std::to_string(plan[p].runs[r].bit3) + " pre=" + std::to_string(plan[p].pre[r]) +
+                       " steps=";
                 for (int i = 0; i < plan[p].runs[r].len; ++i, ++k)
                     out += (i ? "," : "") + std::to_string(plan[p].order[k]);
                 out += "\n";

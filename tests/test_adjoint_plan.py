@@ -1,6 +1,6 @@
 """The fused adjoint sweep's host-side plan (qs_adjoint_describe), checked on
 the CPU without a GPU: every reverse step is scheduled exactly once; within a
-run every non-diagonal step targets one of the run's (at most two) bits, and
+run every non-diagonal step targets one of the run's (at most three) bits, and
 the leading steps a run folds into its load are exchanges on its bits; non-diagonal targets lie in the pass's
 tile; and the scheduled order of U^dagger factors, applied to a random state,
 gives the same vector as the program's reverse order (the reordering only
@@ -34,9 +34,9 @@ def parse(text):
             tile = [int(x) for x in line.split("tile=")[1].split(",")]
             passes.append({"tile": tile, "runs": []})
         elif line.startswith("run "):
-            m = re.match(r"run bit=(-?\d+) bit2=(-?\d+) pre=(\d+) steps=(.*)$", line)
-            passes[-1]["runs"].append({"bit": int(m.group(1)), "bit2": int(m.group(2)), "pre": int(m.group(3)),
-                                       "steps": [int(x) for x in m.group(4).split(",") if x]})
+            m = re.match(r"run bit=(-?\d+) bit2=(-?\d+) bit3=(-?\d+) pre=(\d+) steps=(.*)$", line)
+            passes[-1]["runs"].append({"bit": int(m.group(1)), "bit2": int(m.group(2)), "bit3": int(m.group(3)),
+                                       "pre": int(m.group(4)), "steps": [int(x) for x in m.group(5).split(",") if x]})
     return steps, passes
 
 
@@ -89,10 +89,11 @@ def check_plan(n, dtype, gates, seed):
             assert 0 <= run["pre"] <= len(run["steps"])
             for pos, j in enumerate(run["steps"]):
                 st = steps[j]
+                bits = (run["bit"], run["bit2"], run["bit3"])
                 if pos < run["pre"]:
-                    assert st["cls"] == "x" and st["bit"] in (run["bit"], run["bit2"]), (j, run)
+                    assert st["cls"] == "x" and st["bit"] in bits, (j, run)
                 if st["cls"] != "diag":
-                    assert st["bit"] in (run["bit"], run["bit2"]), (j, run)
+                    assert st["bit"] in bits, (j, run)
                     assert st["bit"] in p["tile"], (j, p["tile"])
                     assert not (st["cmask"] >> st["bit"]) & 1
             if run["bit"] == -1:
@@ -111,23 +112,26 @@ def check_plan(n, dtype, gates, seed):
 
 
 @pytest.mark.parametrize("dtype", ["c64", "c128"])
-@pytest.mark.parametrize("n", [7, 13, 14])
+@pytest.mark.parametrize("n", [11, 13, 14])
 def test_mixed_circuit_plan_is_a_valid_reordering(n, dtype):
     check_plan(n, dtype, mixed_circuit(n, 40 + n), 7 + n)
 
 
-def test_ansatz_runs_group_two_targets():
+def test_ansatz_runs_group_three_targets():
     # the gradient workload's layer reversed: C-NOT(q-1, q), RZ(q), RY(q) share
-    # target q, and a run takes two such targets, so it holds about six steps
+    # target q, and a run takes up to three such targets, so it holds about
+    # nine steps
     n = 13
     gates, _ = W.ansatz_circuit(n, 3, seed=5)
     steps, passes = check_plan(n, "c64", gates, 3)
     runs = [run for p in passes for run in p["runs"]]
-    assert len(runs) <= len(steps) // 4, (len(runs), len(steps))
-    assert sum(1 for run in runs if run["bit2"] >= 0) >= 0.8 * len(runs)
+    assert len(runs) <= len(steps) // 6, (len(runs), len(steps))
+    assert sum(1 for run in runs if run["bit3"] >= 0) >= 0.6 * len(runs)
 
 
-def test_small_registers_have_no_fused_plan():
-    gates, _ = W.ansatz_circuit(5, 2, seed=1)
-    steps, passes = parse(qs.adjoint_describe(5, "c64", gates))
+@pytest.mark.parametrize("n", [5, 10])
+def test_small_registers_have_no_fused_plan(n):
+    # the fused sweep needs a tile of one octet per thread (2^11 amplitudes)
+    gates, _ = W.ansatz_circuit(n, 2, seed=1)
+    steps, passes = parse(qs.adjoint_describe(n, "c64", gates))
     assert len(steps) == len(gates) and passes == []
