@@ -411,6 +411,7 @@ struct PassC64 {
     const POp *ops;
     uint64_t tiles;
     int32_t K, WB, nops, has_xpose;
+    int32_t has_hb, pad_hb;            // an op takes a Hadamard fast path (fast 6 or 7)
     float scale;
     int32_t n;                         // qubits (trajectory mode: state stride 2^n)
     // trajectory mode: per-(trajectory, op) records; trajectory b's record of
@@ -593,7 +594,11 @@ __device__ __forceinline__ void s_reg_op(float2 (&v)[NA], int cls, uint32_t &xm,
 // each op takes its matrix and the XOR of its control values from the
 // trajectory's records, loaded into shared memory when the tile's trajectory
 // changes.
-template <bool TRAJ>
+// HBF: the pass has uncontrolled Hadamard butterflies with fast paths (fast
+// codes 6 and 7).  Passes without them run an instantiation without those
+// branches, whose code and register allocation are those of the plain
+// dispatch (the random-circuit passes measured 1.2% slower with them).
+template <bool TRAJ, bool HBF>
 __global__ void __launch_bounds__(32 << QS_WB64, QS_FUSED_MINBLOCKS) k_fused_c64(float2 *__restrict__ a0,
                                                                        const __grid_constant__ PassC64 P) {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -677,7 +682,7 @@ __global__ void __launch_bounds__(32 << QS_WB64, QS_FUSED_MINBLOCKS) k_fused_c64
                     xm ^= ok ? (1u << tp) : 0u;
                     continue;
                 }
-                if (fast == 6) {   // Hadamard butterfly on a register slot (factor folded into the pass scale)
+                if (HBF && fast == 6) {   // Hadamard butterfly on a register slot (factor folded into the pass scale)
                     if (tp == 0) s_hb<0, NA>(v, xm);
                     else if (tp == 1) s_hb<1, NA>(v, xm);
                     else if (tp == 2) s_hb<2, NA>(v, xm);
@@ -685,7 +690,7 @@ __global__ void __launch_bounds__(32 << QS_WB64, QS_FUSED_MINBLOCKS) k_fused_c64
                     else s_hb<(RB64 > 4 ? 4 : 0), NA>(v, xm);
                     continue;
                 }
-                if (fast == 7) {   // Hadamard butterfly on a lane bit: low lane v + o, high lane o - v
+                if (HBF && fast == 7) {   // Hadamard butterfly on a lane bit: low lane v + o, high lane o - v
                     const int m = 1 << tp;
                     const float sg = ((lane >> tp) & 1) ? -1.f : 1.f;
 #pragma unroll
@@ -1375,6 +1380,8 @@ void convert_c64(const PassDesc<float> &D, const std::vector<FOp<float>> &ops, P
     out.WB = D.WB;
     out.nops = D.nops;
     out.has_xpose = D.has_xpose;
+    out.has_hb = 0;
+    out.pad_hb = 0;
     out.scale = D.scale;
     std::memcpy(out.tile_pos, D.tile_pos, sizeof(out.tile_pos));
     const int WB = D.WB;
@@ -1409,6 +1416,7 @@ void convert_c64(const PassDesc<float> &D, const std::vector<FOp<float>> &ops, P
         if (f.cls == GC_HB && f.rmask == 0 && f.tmask == 0 && f.omask == 0) {
             if (f.type == OP_REG) q.fast = 6;
             else if (f.type == OP_LANE) q.fast = 7;
+            if (q.fast >= 6) out.has_hb = 1;
         }
         if (f.type == OP_XPOSE) {
             // position of each high tile bit in the old tile order
@@ -1469,9 +1477,11 @@ cudaError_t ensure_device_c64(Plan *P, cudaStream_t st) {
         int sms = 0, per_sm = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const size_t smem_max = (size_t(8) << (LB + RB64 + WB64)) + MAX_OPS * sizeof(POp);
-        e = cudaFuncSetAttribute(k_fused_c64<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_max));
+        e = cudaFuncSetAttribute(k_fused_c64<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_max));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_fused_c64<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_max));
         if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_c64<false>, 32 << WB64, smem_max);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_c64<false, false>, 32 << WB64, smem_max);
         if (e != cudaSuccess) return e;
         g = std::max(1, sms * std::max(1, per_sm));
     }
@@ -1485,7 +1495,10 @@ cudaError_t run_passes_c64(qs_state *s, Plan *P) {
         const uint64_t grid = std::min<uint64_t>(D.tiles, uint64_t(P->grid));
         cudaError_t e = P->mark(s->stream, false);
         if (e != cudaSuccess) return e;
-        k_fused_c64<false><<<unsigned(grid), 32u << D.WB, smem, s->stream>>>(static_cast<float2 *>(s->d), D);
+        if (D.has_hb)
+            k_fused_c64<false, true><<<unsigned(grid), 32u << D.WB, smem, s->stream>>>(static_cast<float2 *>(s->d), D);
+        else
+            k_fused_c64<false, false><<<unsigned(grid), 32u << D.WB, smem, s->stream>>>(static_cast<float2 *>(s->d), D);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         e = P->mark(s->stream, true);
@@ -1719,9 +1732,9 @@ qs_status traj_plan_build(int n, const std::vector<HostOp> &ops, int max_ops, Tr
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const size_t smem_max = (size_t(8) << (LB + RB64 + WB64)) + MAX_OPS * (sizeof(POp) + sizeof(TrajRec));
-    cudaError_t e = cudaFuncSetAttribute(k_fused_c64<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_max));
+    cudaError_t e = cudaFuncSetAttribute(k_fused_c64<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_max));
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_c64<true>, 32 << WB64, smem_max);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_c64<true, false>, 32 << WB64, smem_max);
     if (e != cudaSuccess) { delete T; return cuda_fail(e, "trajectory planner: kernel attributes"); }
     T->grid = std::max(1, sms * std::max(1, per_sm));
     *out = T;
@@ -1738,7 +1751,7 @@ cudaError_t traj_plan_run(TrajPlan *T, float2 *states, uint32_t count, const Tra
         D.tiles = D.tiles_per_traj * count;
         const size_t smem = (D.has_xpose ? (size_t(8) << D.K) : 0) + size_t(D.nops) * (sizeof(POp) + sizeof(TrajRec));
         const uint64_t grid = std::min<uint64_t>(D.tiles, uint64_t(T->grid));
-        k_fused_c64<true><<<unsigned(grid), 32u << D.WB, smem, st>>>(states, D);
+        k_fused_c64<true, false><<<unsigned(grid), 32u << D.WB, smem, st>>>(states, D);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
