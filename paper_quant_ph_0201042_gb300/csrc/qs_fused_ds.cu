@@ -7,14 +7,16 @@
 // write of the state per pass.  The tile is the paper's block M_k (Sec.
 // 2.2.1) generalised to any set of fixed index bits.
 //
-// Number format: the state stays complex128 in memory (the paper's double
-// precision, Sec. 2.1).  At the load each amplitude is split into two float
-// pairs (re = rh + rl, im = ih + il, 48 significant bits) with integer
-// instructions, the gates run in double-single arithmetic (qs_ds.cuh: exact
-// products and sums of the high parts by error-free transformations, low
-// parts in single precision) on the single-precision pipe, and the store
-// joins the pairs back into doubles.  Gate matrices come from the plan's
-// double-precision matrices, split on the host.
+// Number format: the state is complex128 in memory (the paper's double
+// precision, Sec. 2.1) before and after a plan runs.  The first pass of a
+// plan splits each amplitude into two float pairs (re = rh + rl, im = ih +
+// il, 48 significant bits) with integer instructions, the gates run in
+// double-single arithmetic (qs_ds.cuh: exact products and sums of the high
+// parts by error-free transformations, low parts in single precision) on the
+// single-precision pipe, and the last pass joins the pairs back into
+// doubles; between the passes of the plan the state holds the float pairs
+// (16 bytes per amplitude, like the complex128).  Gate matrices come from
+// the plan's double-precision matrices, split on the host.
 //
 // The tile lives in shared memory (16 bytes per amplitude, float4), not in
 // registers: a gate is a loop over the thread's pairs with the target bit a
@@ -89,7 +91,11 @@ struct DsPass {
     uint64_t tiles;
     int32_t nops;
     float scale_h, scale_l;     // folded Hadamard factor
-    int32_t pad;
+    // between the passes of one plan the state holds each amplitude as its
+    // float pairs (rh, rl, ih, il: 16 bytes, the size of the complex128): the
+    // first pass splits the doubles, the last joins them back
+    uint8_t in_pairs, out_pairs;
+    uint8_t pad[2];
     uint8_t tile_pos[DK];       // ascending; the first LB are 0 .. LB-1
 };
 
@@ -179,8 +185,13 @@ __global__ void __launch_bounds__(DTHREADS, DMINBLOCKS) k_fused_ds(double2 *__re
         // load: warp w reads rows w, w + 8, ... (512 contiguous bytes each)
 #pragma unroll 4
         for (int r = warp; r < (1 << DH); r += DTHREADS / 32) {
-            const double2 d = a[base | rowoff[r] | uint64_t(lane)];
-            amp[(r << LB) | lane] = st(ds::load(d.x, d.y));
+            const uint64_t gi = base | rowoff[r] | uint64_t(lane);
+            if (P.in_pairs) {
+                amp[(r << LB) | lane] = reinterpret_cast<const float4 *>(a)[gi];
+            } else {
+                const double2 d = a[gi];
+                amp[(r << LB) | lane] = st(ds::load(d.x, d.y));
+            }
         }
         __syncthreads();
         uint32_t xm = 0;   // logical index i sits at amp[i ^ xm]
@@ -233,7 +244,9 @@ __global__ void __launch_bounds__(DTHREADS, DMINBLOCKS) k_fused_ds(double2 *__re
                 ds::mul1(x.rh, x.rl, P.scale_h, P.scale_l, x.rh, x.rl);
                 ds::mul1(x.ih, x.il, P.scale_h, P.scale_l, x.ih, x.il);
             }
-            a[base | rowoff[r] | uint64_t(lane)] = make_double2(ds::join(x.rh, x.rl), ds::join(x.ih, x.il));
+            const uint64_t gi = base | rowoff[r] | uint64_t(lane);
+            if (P.out_pairs) reinterpret_cast<float4 *>(a)[gi] = st(x);
+            else a[gi] = make_double2(ds::join(x.rh, x.rl), ds::join(x.ih, x.il));
         }
         __syncthreads();
     }
@@ -334,6 +347,10 @@ qs_status ds_plan_build(int n, const std::vector<HostOp> &ops, int max_ops, bool
         P->passes.push_back(D);
         P->tables.push_back(std::move(tab));
         P->order.push_back(gp.idx);
+    }
+    for (size_t k = 0; k < P->passes.size(); ++k) {
+        P->passes[k].in_pairs = uint8_t(k > 0);
+        P->passes[k].out_pairs = uint8_t(k + 1 < P->passes.size());
     }
     *out = P;
     return QS_OK;
