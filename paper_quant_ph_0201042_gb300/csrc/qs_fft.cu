@@ -57,6 +57,8 @@ struct ArithStd {                         // plain complex64 / complex128
     static constexpr int RB = sizeof(R) == 4 ? 5 : 4;
     __device__ static V load(const S &a) { return a; }
     __device__ static S store(const V &v) { return v; }
+    __device__ static V from_bits(const S &a) { return a; }   // (no intermediate format)
+    __device__ static S to_bits(const V &v) { return v; }
     __device__ static V add(const V &a, const V &b) { return mk<R>(a.x + b.x, a.y + b.y); }
     __device__ static V sub(const V &a, const V &b) { return mk<R>(a.x - b.x, a.y - b.y); }
     __device__ static V mul(const C &w, const V &x) { return cmul<R>(w, x); }
@@ -78,6 +80,17 @@ struct ArithDS {                          // complex128 in double-single arithme
     static constexpr int RB = 4;
     __device__ static V load(const S &a) { return ds::load(a.x, a.y); }
     __device__ static S store(const V &v) { return make_double2(ds::join(v.rh, v.rl), ds::join(v.ih, v.il)); }
+    // between passes the amplitude's 16 bytes hold its float pairs as they are
+    __device__ static V from_bits(const S &a) {
+        V v;
+        memcpy(&v, &a, sizeof(V));
+        return v;
+    }
+    __device__ static S to_bits(const V &v) {
+        S a;
+        memcpy(&a, &v, sizeof(S));
+        return a;
+    }
     __device__ static V add(const V &a, const V &b) {
         V o;
         ds::add2(a.rh, a.rl, b.rh, b.rl, o.rh, o.rl);
@@ -114,6 +127,9 @@ struct ArithDS {                          // complex128 in double-single arithme
     static Scal scal(double v) { Scal s; ds::split_const(v, s.h, s.l); return s; }
 };
 
+template <typename A> constexpr bool ARITH_PAIRS = false;
+template <> constexpr bool ARITH_PAIRS<ArithDS> = true;
+
 template <typename A>
 struct FftPass {
     const typename A::C *tin;      // w_{2^13}^m (sign of the transform)
@@ -127,6 +143,8 @@ struct FftPass {
     int32_t lane_lo, lane_hi;  // lane digit: lane bits [lane_lo, lane_hi)
     typename A::Scal scale;  // 2^{-L/2} on the last pass, else 1
     bool scaled;             // this pass applies the scale
+    bool in_pairs, out_pairs;  // double-single: the state between passes holds the float pairs (16 bytes
+                               // per amplitude); the first pass splits the doubles, the last joins them
     uint8_t tile_pos[16];    // the K tile bit positions, ascending (0..4 first)
     uint8_t hpos[8];         // global bit of high tile bit i: FFT bits first, then spectators
     typename A::C rt[32];    // w_32^m (sign of the transform)
@@ -273,7 +291,10 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) k_fft_pass(typename A::S *__re
         V v[NA];
         asm volatile("cp.async.wait_all;" ::: "memory");
 #pragma unroll
-        for (int j = 0; j < NA; ++j) v[j] = A::load(sm[lane | (warp << 5) | (uint32_t(j) << (5 + WB))]);
+        for (int j = 0; j < NA; ++j) {
+            const S &x = sm[lane | (warp << 5) | (uint32_t(j) << (5 + WB))];
+            v[j] = P.in_pairs ? A::from_bits(x) : A::load(x);
+        }
         // digit 1: layout-A registers [0, r1)
         if (P.r1 > 0) {
             const uint64_t t0 = ((base | offA) >> lo) & m1 & ((uint64_t(1) << d1b) - 1);
@@ -314,7 +335,8 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) k_fft_pass(typename A::S *__re
 #pragma unroll
             for (int r = 0; r < RB; ++r)
                 if ((j >> r) & 1) o |= uint64_t(1) << P.hpos[r];
-            a[o] = A::store(P.scaled ? A::scale(v[j], P.scale) : v[j]);
+            const V y = P.scaled ? A::scale(v[j], P.scale) : v[j];
+            a[o] = P.out_pairs ? A::to_bits(y) : A::store(y);
         }
     }
 }
@@ -484,6 +506,9 @@ cudaError_t qft_run(qs_state *s, int lo, int L, bool inverse, int64_t *launches)
             P.lo = lo;
             P.scale = scale;
             P.scaled = pb == lo;
+            // double-single passes hand the float pairs to the next pass
+            P.in_pairs = ARITH_PAIRS<A> && &c != &chunks.front();
+            P.out_pairs = ARITH_PAIRS<A> && &c != &chunks.back();
             for (int m = 0; m < 32; ++m) P.rt[m] = rt[m];
             std::vector<int> hb;            // FFT high bits ascending, then spectators
             int lane_bits = 0;
