@@ -506,23 +506,29 @@ template <int T, int NA>
 __device__ __forceinline__ void s_hb(float2 (&v)[NA], uint32_t xm) {
     // the deferred-exchange bit of the slot is the same across the warp: a
     // branch, not a select per amplitude
+    // In place: the difference overwrites one input, and the sum is formed
+    // from it as 2 x - (x - y) (one rounding of the exact 2 x minus the
+    // rounded difference), so each output lands in an input's register and
+    // no register copies are needed where the op dispatch rejoins.
     if ((xm >> T) & 1) {
 #pragma unroll
         for (int j = 0; j < NA; ++j) {
             if ((j >> T) & 1) continue;
             const int j1 = j | (1 << T);
-            const float2 x = v[j], y = v[j1];
-            v[j] = make_float2(y.x - x.x, y.y - x.y);
-            v[j1] = make_float2(x.x + y.x, x.y + y.y);
+            v[j].x = v[j1].x - v[j].x;
+            v[j].y = v[j1].y - v[j].y;
+            v[j1].x = fmaf(2.f, v[j1].x, -v[j].x);
+            v[j1].y = fmaf(2.f, v[j1].y, -v[j].y);
         }
     } else {
 #pragma unroll
         for (int j = 0; j < NA; ++j) {
             if ((j >> T) & 1) continue;
             const int j1 = j | (1 << T);
-            const float2 x = v[j], y = v[j1];
-            v[j] = make_float2(x.x + y.x, x.y + y.y);
-            v[j1] = make_float2(x.x - y.x, x.y - y.y);
+            v[j1].x = v[j].x - v[j1].x;
+            v[j1].y = v[j].y - v[j1].y;
+            v[j].x = fmaf(2.f, v[j].x, -v[j1].x);
+            v[j].y = fmaf(2.f, v[j].y, -v[j1].y);
         }
     }
 }
