@@ -99,14 +99,19 @@ __global__ void __launch_bounds__(RED_THREADS) k_partial(const cplx<R> *__restri
     uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (KIND == RED_NORM || (KIND == RED_PAULI && arg0 == 0)) {
         // sum of sign * |a_i|^2 (a Pauli string of Z and I only flips nothing):
-        // four amplitudes loaded ahead of their sums, for memory parallelism
+        // four amplitudes loaded ahead of their sums, for memory parallelism.
+        // A Z mask within the low 32 index bits (every register up to 32
+        // qubits) takes its sign from one 32-bit population count.
+        const bool z32 = (arg1 >> 32) == 0;
         for (; i + 3 * stride < N; i += 4 * stride) {
             ds::camp v[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) v[u] = lds(a, i + u * stride);
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const float sg = (KIND == RED_PAULI && (__popcll((i + u * stride) & arg1) & 1)) ? -1.f : 1.f;
+                const uint64_t iu = i + u * stride;
+                const int par = z32 ? __popc(uint32_t(iu) & uint32_t(arg1)) : __popcll(iu & arg1);
+                const float sg = (KIND == RED_PAULI && (par & 1)) ? -1.f : 1.f;
                 ar.add(v[u].rh, v[u].rl, v[u].rh, v[u].rl, sg);
                 ar.add(v[u].ih, v[u].il, v[u].ih, v[u].il, sg);
             }
