@@ -414,7 +414,7 @@ def secondary(args, torch, qs, state128, peaks, sms, sm_mhz):
         r = {}
         for name, fn, nbytes in (("norm", lambda: st.norm(), B << n),
                                  ("expect_Z", lambda: st.expect(zstr), B << n),
-                                 ("expect_XZ", lambda: st.expect(xstr), 2 * (B << n)),
+                                 ("expect_XZ", lambda: st.expect(xstr), B << n),
                                  ("inner", lambda: st.inner(other), 2 * (B << n))):
             fn()
             ms = _time(torch, fn, reps=5)

@@ -88,6 +88,7 @@ struct DAcc {
 // kind RED_NORM: sum |a_i|^2
 // kind RED_PROB_BIT: sum over i with (i & arg0) != 0 of |a_i|^2
 // kind RED_PAULI: sum_i conj(a[i ^ arg0]) a[i] (-1)^popcount(i & arg1)
+//   (with arg0 != 0 summed over pairs, each amplitude read once)
 // kind RED_INNER: sum_i conj(a_i) b_i
 template <typename R, int KIND>
 __global__ void __launch_bounds__(RED_THREADS) k_partial(const cplx<R> *__restrict__ a,
@@ -123,20 +124,36 @@ __global__ void __launch_bounds__(RED_THREADS) k_partial(const cplx<R> *__restri
             ar.add(v.ih, v.il, v.ih, v.il, sg);
         }
     }
-    for (; KIND != RED_NORM && !(KIND == RED_PAULI && arg0 == 0) && i < N; i += stride) {
+    if (KIND == RED_PAULI && arg0 != 0) {
+        // A string with X or Y factors pairs i with j = i ^ arg0: each pair is
+        // read once, from the index with the lowest flipped bit clear.  With
+        // c = conj(a_j) a_i and s_i the Z sign of i, the two terms add to
+        // s_i (c + sigma conj(c)), sigma = (-1)^popcount(arg0 & arg1) (the
+        // sign of j relative to i): 2 s_i Re(c), or 2i s_i Im(c).
+        const int b0 = __ffsll(static_cast<long long>(arg0)) - 1;
+        const uint64_t low = (uint64_t(1) << b0) - 1;
+        const bool odd = __popcll(arg0 & arg1) & 1;
+        const bool z32 = (arg1 >> 32) == 0;
+        for (uint64_t p = i; p < N / 2; p += stride) {
+            const uint64_t ii = ((p & ~low) << 1) | (p & low);
+            const ds::camp v = lds(a, ii), w = lds(a, ii ^ arg0);
+            const int par = z32 ? __popc(uint32_t(ii) & uint32_t(arg1)) : __popcll(ii & arg1);
+            const float sg = (par & 1) ? -2.f : 2.f;
+            if (!odd) {
+                ar.add(w.rh, w.rl, v.rh, v.rl, sg);
+                ar.add(w.ih, w.il, v.ih, v.il, sg);
+            } else {
+                ai.add(w.rh, w.rl, v.ih, v.il, sg);
+                ai.add(w.ih, w.il, v.rh, v.rl, -sg);
+            }
+        }
+    }
+    for (; KIND != RED_NORM && KIND != RED_PAULI && i < N; i += stride) {
         if (KIND == RED_PROB_BIT && !(i & arg0)) continue;
         const ds::camp v = lds(a, i);
         if (KIND == RED_PROB_BIT) {
             ar.add(v.rh, v.rl, v.rh, v.rl, 1.f);
             ar.add(v.ih, v.il, v.ih, v.il, 1.f);
-        } else if (KIND == RED_PAULI) {
-            const ds::camp w = lds(a, i ^ arg0);
-            const float sg = (__popcll(i & arg1) & 1) ? -1.f : 1.f;
-            // conj(w) * v
-            ar.add(w.rh, w.rl, v.rh, v.rl, sg);
-            ar.add(w.ih, w.il, v.ih, v.il, sg);
-            ai.add(w.rh, w.rl, v.ih, v.il, sg);
-            ai.add(w.ih, w.il, v.rh, v.rl, -sg);
         } else {  // RED_INNER: conj(v) * w
             const ds::camp w = lds(b, i);
             ar.add(v.rh, v.rl, w.rh, w.rl, 1.f);

@@ -191,6 +191,10 @@ def test_reductions(dtype):
     for _ in range(12):
         p = "".join(r.choice(list("IXYZ"), size=n))
         assert abs(a.expect(p) - oracle.expect_pauli(psi, p)) < 1e-12, p
+    # flips on the lowest and the highest index bit, an odd and an even number
+    # of Y factors (the pair terms add to a real or to an imaginary part)
+    for p in ["X" + "I" * (n - 1), "I" * (n - 1) + "Y", "Y" + "Z" * (n - 1), "XY" + "I" * (n - 2), "YY" + "Z" * (n - 2)]:
+        assert abs(a.expect(p) - oracle.expect_pauli(psi, p)) < 1e-12, p
     assert abs(a.inner(b) - oracle.inner(psi, phi)) < 1e-12
     a.renormalize()
     assert abs(a.norm() - 1) < (1e-14 if dtype == "c128" else 1e-6)
