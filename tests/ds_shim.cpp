@@ -16,6 +16,13 @@ void shim_cmad2(const float *a, const float *x, const float *b, const float *y, 
     const camp o = cmad2(A, X, B, Y);
     out[0] = o.rh; out[1] = o.rl; out[2] = o.ih; out[3] = o.il;
 }
+// out = a*x + b*y with real a, b (only a[0..1], b[0..1] are read)
+void shim_rmad2(const float *a, const float *x, const float *b, const float *y, float *out) {
+    const ccst A = {a[0], a[1], a[2], a[3]}, B = {b[0], b[1], b[2], b[3]};
+    const camp X = {x[0], x[1], x[2], x[3]}, Y = {y[0], y[1], y[2], y[3]};
+    const camp o = rmad2(A, X, B, Y);
+    out[0] = o.rh; out[1] = o.rl; out[2] = o.ih; out[3] = o.il;
+}
 void shim_cmul(const float *d, const float *x, float *out) {
     const ccst D = {d[0], d[1], d[2], d[3]};
     const camp X = {x[0], x[1], x[2], x[3]};

@@ -10,8 +10,9 @@ rational arithmetic (fractions.Fraction), without a GPU:
     2^-47 |d|), h is d truncated to 24 bits; tiny and zero inputs;
   * join: the double nearest h + l (within half a unit in the last place),
     including the case below a power of two where the spacing halves;
-  * the complex 2x2 row a x + b y, the complex product and the butterfly:
-    errors within a few units of 2^-48 of the terms' magnitudes.
+  * the complex 2x2 row a x + b y (also with real a, b: the row of a real
+    gate such as RY), the complex product and the butterfly: errors within a
+    few units of 2^-48 of the terms' magnitudes.
 """
 import ctypes
 import math
@@ -42,6 +43,7 @@ def shim(tmp_path_factory):
     L.shim_join.argtypes = [ctypes.c_float, ctypes.c_float]
     L.shim_join.restype = ctypes.c_double
     L.shim_cmad2.argtypes = [f4] * 5
+    L.shim_rmad2.argtypes = [f4] * 5
     L.shim_cmul.argtypes = [f4] * 3
     L.shim_butterfly.argtypes = [f4, f4]
     L.shim_mul1.argtypes = [ctypes.c_float] * 4 + [f4, f4]
@@ -161,6 +163,37 @@ def test_cmad2_cmul_butterfly_accuracy(shim):
         s = F(abs(x) + abs(y))
         assert abs(val(px[0], px[1]) - (xr + yr)) <= s * F(2) ** -47
         assert abs(val(py[2], py[3]) - (xi - yi)) <= s * F(2) ** -47
+
+
+def test_rmad2_real_row_accuracy(shim):
+    # the row of a real 2x2 gate: a, b real; any imaginary part given is ignored
+    r = np.random.default_rng(5)
+    out = (ctypes.c_float * 4)()
+    for _ in range(1500):
+        a, b = r.standard_normal(2)
+        x, y = (complex(*r.standard_normal(2)) * 10.0 ** r.uniform(-6, 0) for _ in range(2))
+        junk = complex(0.0, float(r.standard_normal()))
+        A, B, X, Y = (ds_of(shim, z) for z in (a + junk, b - junk, x, y))
+        shim.shim_rmad2(arr(A), arr(X), arr(B), arr(Y), out)
+        ar, br = val(A[0], A[1]), val(B[0], B[1])
+        (xr, xi), (yr, yi) = cval(X), cval(Y)
+        scale = F(abs(a) * abs(x) + abs(b) * abs(y))
+        assert abs(val(out[0], out[1]) - (ar * xr + br * yr)) <= scale * F(2) ** -46
+        assert abs(val(out[2], out[3]) - (ar * xi + br * yi)) <= scale * F(2) ** -46
+        assert abs(out[1]) <= float(np.spacing(np.float32(abs(out[0])))) / 2
+        assert abs(out[3]) <= float(np.spacing(np.float32(abs(out[2])))) / 2
+    # a cancelling row: RY(pi/2) on (x, x) gives (0, sqrt(2) x) up to the error bound (the
+    # low-order products are summed in order, so the cancelled row need not be exactly 0)
+    c = 1 / math.sqrt(2)
+    x = complex(0.3, -0.7)
+    C, M, X = ds_of(shim, complex(c, 0)), ds_of(shim, complex(-c, 0)), ds_of(shim, x)
+    shim.shim_rmad2(arr(C), arr(X), arr(M), arr(X), out)
+    assert abs(val(out[0], out[1])) <= F(abs(x)) * F(2) ** -46
+    assert abs(val(out[2], out[3])) <= F(abs(x)) * F(2) ** -46
+    shim.shim_rmad2(arr(C), arr(X), arr(C), arr(X), out)
+    want = 2 * val(C[0], C[1])
+    assert abs(val(out[0], out[1]) - want * val(X[0], X[1])) <= F(abs(x)) * F(2) ** -46
+    assert abs(val(out[2], out[3]) - want * val(X[2], X[3])) <= F(abs(x)) * F(2) ** -46
 
 
 def test_scale_by_a_double_single_constant(shim):
