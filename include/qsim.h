@@ -234,8 +234,9 @@ qs_status qs_prob_qubit(qs_state *s, int q, double *p1);
  * {'I','X','Y','Z'}, character q acting on qubit q.  QS_EINVAL otherwise. */
 qs_status qs_expect(qs_state *s, const char *pauli, double *out);
 
-/* <a|b> = sum_i conj(a_i) b_i.  a and b must have the same n and dtype and
- * the same stream.  QS_EINVAL otherwise. */
+/* <a|b> = sum_i conj(a_i) b_i.  a and b must have the same n and dtype, live
+ * on the same device and use the same stream.  QS_EINVAL otherwise, before
+ * anything is launched. */
 qs_status qs_inner(qs_state *a, qs_state *b, qs_c128 *out);
 
 /* sum_i |alpha_i|^2. */

@@ -394,6 +394,7 @@ qs_status qs_expect(qs_state *s, const char *pauli, double *out) {
 qs_status qs_inner(qs_state *a, qs_state *b, qs_c128 *out) {
     if (!a || !b || !out) return fail(QS_EINVAL, "NULL argument");
     if (a->n != b->n || a->dt != b->dt) return fail(QS_EINVAL, "states differ in size or dtype");
+    if (a->device != b->device) return fail(QS_EINVAL, "states are on different devices");
     if (a->stream != b->stream) return fail(QS_EINVAL, "states are on different streams");
     return reduce_to_host(a, RED_INNER, 0, 0, b->d, &out->re, &out->im);
 }
